@@ -1,0 +1,143 @@
+"""Pins for the oracle's right-hand side, time integrator and norms (no GPU)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from synth import unit_square_mesh, heat_sin_mode, manufactured_dirichlet, PERIODIC, DIRICHLET
+from oracle.mesh import Mesh
+from oracle.rhs import Problem, error_norms, stable_dt
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _poly(N, seed):
+    rng = np.random.default_rng(seed)
+    co = {(a, b): rng.standard_normal() for a in range(N + 1) for b in range(N + 1 - a)}
+    f = lambda x, y: sum(c * x ** a * y ** b for (a, b), c in co.items()) + 0 * x
+    fx = lambda x, y: sum(c * a * x ** (a - 1) * y ** b for (a, b), c in co.items() if a) + 0 * x
+    fy = lambda x, y: sum(c * b * x ** a * y ** (b - 1) for (a, b), c in co.items() if b) + 0 * x
+    lap = lambda x, y: (sum(c * a * (a - 1) * x ** (a - 2) * y ** b for (a, b), c in co.items() if a > 1)
+                        + sum(c * b * (b - 1) * x ** a * y ** (b - 2) for (a, b), c in co.items() if b > 1) + 0 * x)
+    return f, fx, fy, lap
+
+
+def _unwrapped_elements(m):
+    good = np.ones(m.K, bool)
+    for (k1, f1, k2, f2, sx, sy) in m.edges:
+        if abs(sx) + abs(sy) > 1e-12:
+            good[k1] = good[k2] = False
+    return good
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_rhs_exact_for_global_polynomials(N):
+    """rhs = D lap p - v.grad p at the nodes of every element whose edges are not wrapped."""
+    xy, tri = unit_square_mesh(5, 0.1, 4)
+    m = Mesh(xy, tri, N)
+    D, v = 0.37, (0.8, -0.45)
+    pr = Problem(m, np.full(m.K, D), v=v)
+    f, fx, fy, lap = _poly(N, 100 + N)
+    r = pr.rhs(f(m.x, m.y))
+    want = D * lap(m.x, m.y) - v[0] * fx(m.x, m.y) - v[1] * fy(m.x, m.y)
+    good = _unwrapped_elements(m)
+    scale = 1 + np.abs(want).max()
+    assert np.abs(r - want)[good].max() < 1e-9 * scale * (N + 1) ** 4
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_rhs_zero_for_linear_and_constant_data(N):
+    xy, tri = unit_square_mesh(5, 0.1, 6)
+    m = Mesh(xy, tri, N)
+    good = _unwrapped_elements(m)
+    lin = 0.3 + 1.7 * m.x - 0.9 * m.y
+    tol = 1e-13 * (N + 1) ** 4 * 25 * 3     # roundoff of an operator of norm ~ (N+1)^4 / h^2
+    pr = Problem(m, np.full(m.K, 0.6))
+    assert np.abs(pr.rhs(lin))[good].max() < tol
+    # constants are steady for any element-wise D (L 1 = 0 everywhere)
+    pr = Problem(m, np.random.default_rng(0).uniform(0.1, 1, m.K), v=(0.2, 0.7))
+    assert np.abs(pr.rhs(np.full((m.K, m.ops.Np), 2.5))).max() < tol
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 6])
+def test_conservation_periodic(N):
+    """sum_k J_k 1^T M rhs_k = 0: the interface flux is single valued."""
+    xy, tri = unit_square_mesh(5, 0.1, 8)
+    m = Mesh(xy, tri, N)
+    pr = Problem(m, np.random.default_rng(1).uniform(1e-3, 1, m.K), v=(0.4, 0.9))
+    u = np.random.default_rng(2).standard_normal((m.K, m.ops.Np))
+    r = pr.rhs(u)
+    total = np.sum(m.J[:, None] * (r @ m.ops.M))
+    assert abs(total) < 1e-12 * np.sum(np.abs(m.J[:, None] * (r @ m.ops.M)))
+
+
+@pytest.mark.parametrize("msz,N", [(2, 2), (3, 1)])
+def test_dense_operator_stable_and_rk3_amplification(msz, N):
+    xy, tri = unit_square_mesh(msz, 0.1, 5)
+    m = Mesh(xy, tri, N)
+    pr = Problem(m, np.full(m.K, 1.0), v=(0.3, 0.2))
+    Lop = pr.dense_operator()
+    lam, vec = np.linalg.eig(Lop)
+    rho = np.abs(lam).max()
+    assert lam.real.max() <= 1e-10 * rho
+    # SSP-RK3 on an eigenvector multiplies it by 1 + z + z^2/2 + z^3/6 exactly
+    j = int(np.argmax(np.abs(lam)))
+    z0 = lam[j]
+    dt = 0.5 / abs(z0)
+    x = np.real(vec[:, j] / vec[np.argmax(np.abs(vec[:, j])), j])
+    if np.abs(np.imag(z0)) > 1e-9 * abs(z0):
+        pytest.skip("dominant eigenvalue complex")
+    z = z0.real * dt
+    y = pr.rk3_step(x.reshape(m.K, -1), 0.0, dt).ravel()
+    assert np.allclose(y, (1 + z + z * z / 2 + z ** 3 / 6) * x, atol=1e-9 * np.abs(x).max())
+
+
+def test_heat_sin_mode_decay_rate():
+    """Config-1 workload: sin(2 pi x) sin(2 pi y) decays as exp(-8 pi^2 D t); the discrete
+    decay rate matches to 1e-2 on m = 16 and the error shrinks on m = 32."""
+    errs = []
+    for mm in (16, 32):
+        w = heat_sin_mode(m=mm)
+        me = Mesh(w.xy, w.tri, w.N)
+        pr = Problem(me, w.D_elem)
+        u0 = w.u0(me.x, me.y)
+        T = w.steps * w.dt
+        uT = pr.solve(u0, 0.0, w.dt, w.steps)
+        Mw = me.J[:, None] * (u0 @ me.ops.M)
+        rate = math.log(np.sum(Mw * uT) / np.sum(Mw * u0)) / (-8 * math.pi ** 2 * T)
+        errs.append(abs(rate - 1.0))
+        assert abs(rate - 1.0) < 1e-2
+    assert errs[1] < errs[0]
+
+
+def test_manufactured_dirichlet_convergence_order():
+    """N = 3 manufactured solution with Dirichlet ghosts: observed L2 order near P+1 = 4
+    (the paper's P3 orders in Table purediff_ooa are 4.005/4.018/4.005)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "purediff_ooa.txt")) if l[0] != "#"]
+    p3 = [float(r[3]) for r in rows]
+    errs = []
+    for mm in (4, 8, 16):
+        w = manufactured_dirichlet(mm, N=3)
+        me = Mesh(w.xy, w.tri, w.N, bc=DIRICHLET)
+        src = [(f(me.x, me.y), k, o) for f, k, o in zip(w.source.funcs, w.source.kinds, w.source.omegas)]
+        pr = Problem(me, w.D_elem, source=src, ghost_fn=w.exact)
+        T = w.meta["T"]
+        dt = stable_dt(pr, 0.5, 30)
+        n = int(math.ceil(T / dt))
+        uT = pr.solve(w.exact(me.x, me.y, 0.0), 0.0, T / n, n)
+        errs.append(error_norms(me, uT, w.exact, T)[0])
+    order = math.log2(errs[1] / errs[2])
+    assert abs(order - np.mean(p3)) < 0.3
+
+
+def test_error_norms_on_exact_interpolant():
+    """Norms vanish for a polynomial of degree <= N and match a hand value for a constant
+    offset (L2 = L_inf = offset)."""
+    xy, tri = unit_square_mesh(4, 0.1, 1)
+    m = Mesh(xy, tri, 3)
+    f = lambda x, y, t: 1 + x * y * y - 2 * x ** 3
+    l2, li = error_norms(m, f(m.x, m.y, 0), f, 0.0)
+    assert l2 < 1e-13 and li < 1e-13
+    l2, li = error_norms(m, f(m.x, m.y, 0) + 0.25, f, 0.0)
+    assert abs(l2 - 0.25) < 1e-13 and abs(li - 0.25) < 1e-13
