@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput of the reconstructed-DG convection-diffusion solve on GB300.
+
+One bench step = one full solve of the single-GPU workload: N = 4 (Np = 15) nodal DG on a
+256 x 256 x 2 jittered periodic mesh (131072 triangles, seed 1), v = (1, 0.5), D = 1 inside
+the circle r < 0.25 about (0.5, 0.5) and 1e-4 outside, Gaussian pulse of width 0.05,
+500 SSP-RK3 steps (1500 right-hand sides) at 0.5 x the stability bound, FP32 arithmetic.
+The metric is GDOF/s = K Np x (right-hand sides) / time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank runs an independent replica (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.  --impl reference times the FP64 NumPy oracle on
+the host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "recDG diffusion RHS GDOF/s, FP32 vs FP64 at stated L2 err; serve p50/p99"
+UNIT = "GDOF/s"
+N_ORDER = 4
+RK_STEPS = 500
+ORACLE_SAMPLE_M = 64
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=256, help="mesh side (cells)")
+    p.add_argument("--rk-steps", type=int, default=RK_STEPS)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_sample_gdofs(seconds_budget=12.0, m=ORACLE_SAMPLE_M):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the same
+    recipe on an m x m x 2 mesh, setup excluded, SSP-RK3 steps until the budget is used."""
+    from synth import circle_pulse
+    from oracle.mesh import Mesh
+    from oracle.rhs import Problem
+    w = circle_pulse(m=m, N=N_ORDER)
+    me = Mesh(w.xy, w.tri, w.N)
+    pr = Problem(me, w.D_elem, v=w.v)
+    u = w.u0(me.x, me.y)
+    dt = 1e-7
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        u = pr.rk3_step(u, n * dt, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or n >= 400:
+            break
+    gd = me.K * me.ops.Np * 3 * n / el / 1e9
+    return gd, {"kind": "oracle", "cores": 1, "sample": "FP64 NumPy oracle, same recipe on %dx%dx2 = %d triangles "
+                "(1/%d of the workload), %d SSP-RK3 steps = %d right-hand sides, %.1f s, setup excluded, "
+                "BLAS pinned to 1 thread" % (m, m, me.K, (256 // m) ** 2, n, 3 * n, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import circle_pulse
+    from oracle.mesh import Mesh
+    from oracle.rhs import Problem
+    w = circle_pulse(m=ORACLE_SAMPLE_M, N=N_ORDER)
+    me = Mesh(w.xy, w.tri, w.N)
+    pr = Problem(me, w.D_elem, v=w.v)
+    u = w.u0(me.x, me.y)
+    dt = 1e-7
+    per_step = 8           # RK steps of the sample in one bench step
+    for i in range(args.warmup):
+        for j in range(per_step):
+            u = pr.rk3_step(u, 0.0, dt)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        for j in range(per_step):
+            u = pr.rk3_step(u, 0.0, dt)
+    el = time.perf_counter() - t0
+    val = me.K * me.ops.Np * 3 * per_step * args.steps / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": "FP64 NumPy oracle, same recipe on %dx%dx2 = %d triangles, %d SSP-RK3 "
+                                       "steps per bench step, setup excluded, BLAS pinned to 1 thread"
+                                       % (ORACLE_SAMPLE_M, ORACLE_SAMPLE_M, me.K, per_step)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": "circle_pulse N=4 (Np=15), %dx%dx2=%d jittered periodic triangles (seed 1), v=(1,0.5), "
+                        "D=1 in r<0.25 else 1e-4, Gaussian w=0.05, %d SSP-RK3 steps at 0.5x stability bound"
+                        % (args.m, args.m, 2 * args.m * args.m, args.rk_steps),
+            "N": N_ORDER, "triangles": 2 * args.m * args.m, "rk_steps_per_bench_step": args.rk_steps,
+            "rhs_per_bench_step": 3 * args.rk_steps, "precision": "fp32",
+            "l2_flush": "256 MB buffer written between timed steps (outside the events)",
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+# ---------------------------------------------------------------------------------------
+def spectral_radius(s, torch, iters=50, seed=0):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.randn((s.K, s.Np), generator=g, device="cuda", dtype=s.dtype)
+    y = torch.empty_like(x)
+    rho = 0.0
+    for _ in range(iters):
+        x /= torch.linalg.vector_norm(x)
+        s.rhs_eval(x, y, 0.0)
+        rho = float(torch.linalg.vector_norm(y))
+        x, y = y, x
+    return rho
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_1912_06221_gb300 as rdg
+    rdg.load()
+    from synth import circle_pulse
+    w = circle_pulse(m=args.m, N=N_ORDER)
+    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32, device=local)
+    stream = torch.cuda.current_stream()
+    xyn = s.node_coords()
+    u0_host = w.u0(xyn[..., 0], xyn[..., 1]).astype(np.float32)
+    u0 = torch.tensor(u0_host, device="cuda")
+    rho = spectral_radius(s, torch)
+    dt = 0.5 * 2.5127 / rho
+    nrk = args.rk_steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        s.set_state(u0)
+        s.solve_to_time(0.0, dt, nrk)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.set_state(u0)
+        s.solve_to_time(0.0, dt, nrk)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt)
+    dofs = s.K * s.Np * 3 * nrk * args.steps * world
+    value = dofs / (t_ms / 1e3) / 1e9
+    u_fp32 = s.get_state_host().astype(np.float64)
+
+    # per-kernel times (event-bracketed launches of one more solve)
+    s.profile(True)
+    s.set_state(u0)
+    s.solve_to_time(0.0, dt, 100)
+    st = s.kernel_stats()
+    s.profile(False)
+    edge_n, edge_ms = st["edge"]
+    elem_n, elem_ms = st["elem"]
+    E, K, Np, Nfp = s.E, s.K, s.Np, s.Nfp
+    edge_bytes = E * (Nfp * 2 * Np * 4 + 8 + Nfp * 4) + K * Np * 4
+    elem_bytes = K * (3 * Np * 4 + 6 * 4 + 12) + E * Nfp * 4
+    peak, peak_kind = measured_peaks()
+    edge_avg = edge_ms / edge_n
+    elem_avg = elem_ms / elem_n
+    ach = edge_bytes / (edge_avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "edge_flux_kernel<float,4>", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+            "alg_bytes_per_launch": edge_bytes, "avg_launch_us": edge_avg * 1e3,
+            "share_of_kernel_time": edge_ms / (edge_ms + elem_ms),
+            "elem_kernel": {"alg_bytes_per_launch": elem_bytes, "avg_launch_us": elem_avg * 1e3,
+                            "achieved_gbs": elem_bytes / (elem_avg / 1e3) / 1e9},
+            "stage_roofline_frac": (edge_bytes + elem_bytes) / ((edge_avg + elem_avg) / 1e3) / 1e9 / peak}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e_t = []
+    out_host = np.empty_like(u0_host)
+    for i in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_state(u0_host)
+        s.solve_to_time(0.0, dt, nrk)
+        out_host[...] = s.get_state_host()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = s.K * s.Np * 3 * nrk * world / (float(np.mean(e2e_t))) / 1e9
+
+    fp64 = None
+    if not args.no_fp64:
+        s64 = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP64, device=local)
+        u064 = torch.tensor(w.u0(xyn[..., 0], xyn[..., 1]), device="cuda")
+        s64.set_state(u064)
+        s64.solve_to_time(0.0, dt, 16)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s64.set_state(u064)
+        a.record(stream)
+        s64.solve_to_time(0.0, dt, nrk)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b)
+        u64 = s64.get_state_host()
+        l2 = float(np.linalg.norm(u_fp32 - u64) / np.linalg.norm(u64))
+        linf = float(np.abs(u_fp32 - u64).max() / np.abs(u64).max())
+        fp64 = {"value": s.K * s.Np * 3 * nrk / (t64 / 1e3) / 1e9, "unit": UNIT,
+                "fp32_rel_l2_vs_fp64": l2, "fp32_rel_linf_vs_fp64": linf, "t_final": nrk * dt}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gd, meta = oracle_sample_gdofs()
+        cpu = dict(value=gd, unit=UNIT, **meta)
+
+    per_solve = (1 + (nrk // 16) * (16 * 6 + 1) if nrk >= 16 else 0) + (nrk % 16) * 6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args), "dt": dt, "rho": rho,
+            "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
+                    "d2h_bytes_per_step": int(out_host.nbytes)},
+            "gpu_launches": per_solve * args.steps,
+            "fp64_gpu": fp64}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

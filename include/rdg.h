@@ -1,0 +1,168 @@
+/*
+ * rdg.h -- C ABI of the GB300 (sm_103a) affine reconstructed nodal DG library.
+ *
+ * Method: Song & Srinivasan, "An efficient reconstruction algorithm for diffusion on
+ * triangular grids using the nodal discontinuous Galerkin method" (arXiv 1912.06221).
+ * The library evaluates the semi-discrete right-hand side of
+ *
+ *     u_t + div(v u) - div(D grad u) = s                       (Eq. convection_diffusion)
+ *
+ * on a triangle mesh in the reference-domain form of Eq.
+ * NDG_diffusion_once_matrixForm_Fullyreference: a volume term M^{-1} S^T . F with
+ * F = v u - D grad u, and surface terms (J_f / J) LIFT_f (F*.n) whose diffusive part is the
+ * normal gradient of the polynomial reconstructed on the enclosed parallelogram of each
+ * interior edge (Sec. 4, Algorithm aRDG).  Element-wise D uses Algorithm 2 (D~ = RDG(D1,D2)).
+ * Time stepping is the three-stage SSP-RK3 scheme.
+ *
+ * Conventions shared with every caller:
+ *  - order N in 1..6; Np = (N+1)(N+2)/2 nodes per triangle, Nfp = N+1 per face.
+ *  - nodes: Warp & Blend points with alpha = 0 on the reference triangle
+ *    {r,s >= -1, r+s <= 0} with vertices v1=(-1,-1), v2=(1,-1), v3=(-1,1), ordered row by
+ *    row (for i = 0..N, for j = 0..N-i); element vertex k maps to v_k through the affine map
+ *    x = -(r+s)/2 x1 + (r+1)/2 x2 + (s+1)/2 x3 (Eq. mapping_tri).
+ *  - nodal arrays are row-major [K][Np] (element-major), in the precision chosen at
+ *    rdg_operator_setup (double for RDG_FP64, float for RDG_FP32).
+ *  - triangles must be counter-clockwise; faces are (x1,x2), (x2,x3), (x3,x1).
+ *
+ * Status: every call returns 0 (RDG_OK) or a negative RDG_E* code; rdg_last_error() gives a
+ * message.  Ownership: host arrays passed in are copied and stay the caller's; device
+ * pointers passed in are borrowed for the duration of the call (work is enqueued on the
+ * context's stream, so they must stay valid until that stream reaches it) and are never
+ * freed by the library; the library owns and frees everything it allocates in
+ * rdg_destroy.  Threading: one context per host thread at a time; all device work of a
+ * context runs on its stream.
+ */
+#ifndef RDG_H
+#define RDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rdg_ctx rdg_ctx;
+
+enum {
+  RDG_OK = 0,
+  RDG_EINVAL = -1,   /* bad argument (range, null pointer, size) */
+  RDG_ENOMEM = -2,   /* device or host allocation failed */
+  RDG_ECUDA = -3,    /* a CUDA runtime call failed */
+  RDG_EMESH = -4,    /* mesh not valid: clockwise/degenerate triangle, non-manifold or unmatched edge */
+  RDG_ERANK = -5,    /* reconstruction system not of full column rank */
+  RDG_ETIMEOUT = -6, /* a bounded device wait gave up */
+  RDG_ESTATE = -7    /* call made in the wrong order (e.g. rhs before operator setup) */
+};
+
+enum { RDG_BC_PERIODIC = 0, RDG_BC_DIRICHLET = 1 };
+enum { RDG_FP64 = 0, RDG_FP32 = 1 };
+enum { RDG_TAU_CONST = 0, RDG_TAU_COS = 1, RDG_TAU_SIN = 2 };
+#define RDG_MAX_FORCING_TERMS 4
+
+/* Library version string. */
+const char* rdg_version(void);
+
+/* Message for the last failing call on ctx (or for rdg_create when ctx is NULL). */
+const char* rdg_last_error(const rdg_ctx* ctx);
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run on (the
+ * legacy default stream, cudaStreamLegacy, is accepted), or NULL for a stream the library
+ * creates (non-blocking) and destroys.  Graphs are captured on a private stream and
+ * launched on this one.  Also uploads the
+ * reference operators of every order to the device on first use of that device.
+ * Errors: RDG_EINVAL (device out of range), RDG_ECUDA, RDG_ENOMEM. */
+int rdg_create(rdg_ctx** out, int device, void* cuda_stream);
+
+/* Free every buffer the context owns and the context itself (NULL is accepted). */
+int rdg_destroy(rdg_ctx* ctx);
+
+/* Mesh: nv vertices xy[2*nv] (x0,y0,x1,y1,...), nt counter-clockwise triangles tri[3*nt]
+ * (0-based vertex ids).  bc = RDG_BC_PERIODIC: every face must meet another face whose
+ * midpoint agrees modulo period[0..1] (period must be non-NULL); the neighbour's vertex
+ * coordinates are translated onto the shared face.  bc = RDG_BC_DIRICHLET: faces met by no
+ * other face are boundary edges whose outer side is the ghost triangle, the point
+ * reflection of the element about the edge midpoint (period may be NULL).
+ * Errors: RDG_EINVAL, RDG_EMESH (non-CCW or degenerate triangle, an edge shared by more
+ * than two faces, an unmatched periodic face), RDG_ENOMEM. */
+int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                    int32_t bc, const double* period);
+
+/* Operators for order N (1..6) with element-wise diffusion D_elem[nt] (> 0), constant
+ * velocity (vx, vy), arithmetic precision RDG_FP64 or RDG_FP32.  Builds, in FP64 on the GPU,
+ * the element metric terms and for every edge the enclosed parallelogram (Sec. 4.2), the
+ * projections V^{-1} V_p V_rf^{-1} of both sides (Eq. totalProjection), the least-squares
+ * reconstruction (Sec. 4.5) and the edge-normal gradient, folded with D~ = RDG(D1, D2)
+ * (Algorithm 2), the edge Jacobian J_f and the upwind convective trace into one
+ * Nfp x 2Np flux operator per edge, stored in the chosen precision.
+ * Errors: RDG_ESTATE (no mesh), RDG_EINVAL, RDG_ERANK, RDG_ENOMEM, RDG_ECUDA. */
+int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision);
+
+/* Separable forcing (after rdg_operator_setup).  Source s(x,t) = sum_m S_m(x) tau_m(t) with
+ * S given as nodal values S[nsrc][nt][Np] (host, double), tau_m = 1, cos(w t) or sin(w t)
+ * per src_kind[m], src_omega[m].  Dirichlet ghost data g(x,t) = sum_m G_m(x) tau_m(t) with
+ * G[nghost][nb][Np] (host, double) at the ghost nodes returned by rdg_get_ghost_coords.
+ * nsrc, nghost <= RDG_MAX_FORCING_TERMS; 0 clears.  Errors: RDG_ESTATE, RDG_EINVAL. */
+int rdg_set_forcing(rdg_ctx* ctx, int nsrc, const double* S, const int32_t* src_kind, const double* src_omega,
+                    int nghost, const double* G, const int32_t* ghost_kind, const double* ghost_omega);
+
+/* Counts after rdg_mesh_upload: triangles, edges (interior + boundary), boundary edges. */
+int rdg_mesh_counts(const rdg_ctx* ctx, int64_t* nt, int64_t* n_edges, int64_t* n_boundary);
+
+/* Physical node coordinates xy[nt][Np][2] (host, double) after rdg_operator_setup. */
+int rdg_get_node_coords(rdg_ctx* ctx, double* xy);
+
+/* Ghost-triangle node coordinates xy[nb][Np][2] (host, double) of the boundary edges, in the
+ * order rdg_set_forcing expects G. */
+int rdg_get_ghost_coords(rdg_ctx* ctx, double* xy);
+
+/* Resident state u[nt][Np] in the context's precision; on_device != 0: u is a device
+ * pointer (copied device to device), else a host pointer.  Errors: RDG_ESTATE, RDG_EINVAL. */
+int rdg_set_state(rdg_ctx* ctx, const void* u, int on_device);
+int rdg_get_state(rdg_ctx* ctx, void* out, int to_device);
+
+/* rhs = L(u, t) for device arrays u, rhs [nt][Np] in the context's precision (no host
+ * synchronisation; enqueued on the context's stream).  Both must be 16-byte aligned and must
+ * not overlap (RDG_EINVAL otherwise). */
+int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
+
+/* One SSP-RK3 step of the resident state from time t with step dt (stages at t, t+dt,
+ * t+dt/2); enqueued, no host synchronisation. */
+int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
+
+/* nsteps SSP-RK3 steps of the resident state from t0 with step dt, replayed from a CUDA
+ * graph of a fixed chunk of steps (captured on first use for a given dt); enqueued. */
+int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps);
+
+/* Per-kernel timing.  With enable != 0 every later edge-flux and element-update kernel launch
+ * of ctx is bracketed by CUDA events on the context stream (rdg_solve_to_time then steps
+ * without its graph).  rdg_kernel_stats waits for the stream and returns, for kernel class
+ * 0 (edge flux) and 1 (element update), the number of launches and the summed device
+ * milliseconds since the last reset; reset != 0 clears them afterwards. */
+int rdg_profile(rdg_ctx* ctx, int enable);
+int rdg_kernel_stats(rdg_ctx* ctx, int64_t* launches, double* ms, int reset);
+
+/* Wait for the context's stream; returns RDG_ECUDA if device work failed. */
+int rdg_synchronize(rdg_ctx* ctx);
+
+/* Device bytes a context allocates for order N, nt triangles, n_edges edges (n_boundary of
+ * them boundary edges), precision, nsrc/nghost forcing terms: the admission figure a
+ * scheduler compares with its memory budget. */
+int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int precision, int nsrc, int nghost,
+                    int64_t* bytes);
+
+/* Reference operators of order N as the library computed them (host FP64), for checks:
+ * which = 0 nodes r,s [2][Np]; 1 Dr [Np][Np]; 2 Ds; 3 LIFT [Np][3 Nfp]; 4 pseudo-inverse of
+ * the reconstruction system [Mp][2Np]; 5 mass matrix [Np][Np].  out must hold the
+ * stated number of doubles. */
+int rdg_reference_operator(int N, int which, double* out);
+
+/* Per-edge flux operators in FP64 as built on the GPU: W[n_edges][Nfp][2Np] (host,
+ * double), plus per edge (k1, f1, k2, f2) into ids[n_edges][4] (k2 = -1-b for the b-th
+ * boundary edge).  For checks and tooling; not needed for solving. */
+int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDG_H */

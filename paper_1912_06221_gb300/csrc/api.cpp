@@ -1,0 +1,819 @@
+// C ABI of the aRDG library: context, mesh connectivity, operator setup, forcing, state,
+// right-hand side, SSP-RK3 stepping and CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+using namespace rdg;
+
+struct EdgeRec {
+  int32_t k1, f1, k2, f2;  // k2 = -1 - b for boundary edge b
+  double shx, shy;
+};
+
+struct rdg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;     // the caller's stream (may be the legacy default stream)
+  cudaStream_t cap_stream = nullptr; // private stream used only to capture graphs
+  bool capturing = false;
+  bool own_stream = false;
+  std::string err;
+  // mesh (host)
+  bool mesh_ok = false;
+  int64_t K = 0, E = 0, B = 0;
+  int bc = 0;
+  std::vector<double> exy;       // [K][6]
+  std::vector<EdgeRec> edges;    // interior edges first, then boundary edges
+  std::vector<int32_t> eref;     // [3][K]
+  // operators
+  bool ops_ok = false;
+  int N = 0, prec = RDG_FP32, esz = 4;
+  double vx = 0, vy = 0;
+  std::vector<double> Dk;
+  // device buffers
+  void* d_W = nullptr;
+  int32_t *d_k1 = nullptr, *d_k2 = nullptr, *d_eref = nullptr;
+  void *d_geo = nullptr, *d_flux = nullptr, *d_u = nullptr, *d_u1 = nullptr, *d_u2 = nullptr;
+  void *d_S = nullptr, *d_G = nullptr;
+  TimeState* d_time = nullptr;
+  Forcing frc;
+  // per-kernel event timing (class 0 edge flux, 1 element update)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[2];
+  double prof_ms[2] = {0, 0};
+  int64_t prof_n[2] = {0, 0};
+  // graph of a chunk of steps for one dt
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = 0;
+  int g_chunk = 0;
+};
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_create_err;
+std::mutex g_tab_mu;
+std::vector<bool> g_tab_uploaded;
+
+int fail(rdg_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_err = msg;
+  }
+  return code;
+}
+
+int cuda_fail(rdg_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? RDG_ENOMEM : RDG_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);  \
+  } while (0)
+
+void dfree(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_ops(rdg_ctx* ctx) {
+  dfree(ctx->d_W);
+  dfree(ctx->d_k1);
+  dfree(ctx->d_k2);
+  dfree(ctx->d_eref);
+  dfree(ctx->d_geo);
+  dfree(ctx->d_flux);
+  dfree(ctx->d_u);
+  dfree(ctx->d_u1);
+  dfree(ctx->d_u2);
+  dfree(ctx->d_S);
+  dfree(ctx->d_G);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  ctx->ops_ok = false;
+  ctx->frc = Forcing();
+}
+
+cudaEvent_t take_event(rdg_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Sum the elapsed times of completed event pairs (the caller has synchronised the stream).
+void drain_events(rdg_ctx* ctx) {
+  for (int c = 0; c < 2; ++c) {
+    for (auto& pr : ctx->ev_pending[c]) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        ctx->prof_ms[c] += ms;
+        ctx->prof_n[c] += 1;
+      }
+      ctx->ev_pool.push_back(pr.first);
+      ctx->ev_pool.push_back(pr.second);
+    }
+    ctx->ev_pending[c].clear();
+  }
+}
+
+void free_events(rdg_ctx* ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  drain_events(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  ctx->ev_pool.clear();
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int64_t w_bytes(int N, int64_t E, int esz) {
+  const int64_t tiles = (E + kTile - 1) / kTile;
+  return tiles * w_vecs_per_edge(N, esz) * kTile * 16;
+}
+
+const int kFaceA[3] = {0, 1, 2}, kFaceB[3] = {1, 2, 0};
+
+}  // namespace
+
+extern "C" {
+
+const char* rdg_version(void) { return "rdg-gb300 0.1 (sm_103a)"; }
+
+const char* rdg_last_error(const rdg_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_create_err.c_str();
+}
+
+int rdg_create(rdg_ctx** out, int device, void* cuda_stream) {
+  if (!out) return fail(nullptr, RDG_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return fail(nullptr, RDG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  if (device < 0 || device >= n) return fail(nullptr, RDG_EINVAL, "device out of range");
+  DeviceGuard g(device);
+  {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if ((int)g_tab_uploaded.size() < n) g_tab_uploaded.resize(n, false);
+    if (!g_tab_uploaded[device]) {
+      for (int N = 1; N <= kMaxN; ++N) {
+        const char* msg = "";
+        if (!get_refops(N, &msg)) return fail(nullptr, RDG_ERANK, msg);
+      }
+      if (upload_elem_tables(device) != RDG_OK)
+        return fail(nullptr, RDG_ECUDA, "uploading reference operators failed");
+      g_tab_uploaded[device] = true;
+    }
+  }
+  rdg_ctx* c = new (std::nothrow) rdg_ctx();
+  if (!c) return fail(nullptr, RDG_ENOMEM, "host allocation failed");
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, RDG_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  e = cudaMalloc(&c->d_time, sizeof(TimeState));
+  if (e != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return fail(nullptr, RDG_ENOMEM, "device allocation failed");
+  }
+  *out = c;
+  return RDG_OK;
+}
+
+int rdg_destroy(rdg_ctx* ctx) {
+  if (!ctx) return RDG_OK;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_ops(ctx);
+  free_events(ctx);
+  dfree(ctx->d_time);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return RDG_OK;
+}
+
+int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri, int32_t bc,
+                    const double* period) {
+  if (!ctx) return RDG_EINVAL;
+  if (nv <= 0 || nt <= 0 || !xy || !tri) return fail(ctx, RDG_EINVAL, "empty mesh or NULL arrays");
+  if (nt > (int64_t)1 << 30) return fail(ctx, RDG_EINVAL, "too many triangles (max 2^30)");
+  if (bc != RDG_BC_PERIODIC && bc != RDG_BC_DIRICHLET) return fail(ctx, RDG_EINVAL, "bc must be PERIODIC or DIRICHLET");
+  if (bc == RDG_BC_PERIODIC && (!period || !(period[0] > 0) || !(period[1] > 0)))
+    return fail(ctx, RDG_EINVAL, "periodic mesh needs a positive period");
+  free_ops(ctx);
+  ctx->mesh_ok = false;
+  ctx->K = nt;
+  ctx->bc = bc;
+  ctx->exy.assign(nt * 6, 0.0);
+  double hmin = 1e300;
+  for (int64_t k = 0; k < nt; ++k) {
+    for (int c = 0; c < 3; ++c) {
+      int32_t v = tri[3 * k + c];
+      if (v < 0 || v >= nv) return fail(ctx, RDG_EMESH, "vertex id out of range in triangle " + std::to_string(k));
+      ctx->exy[6 * k + 2 * c] = xy[2 * v];
+      ctx->exy[6 * k + 2 * c + 1] = xy[2 * v + 1];
+    }
+    const double* p = &ctx->exy[6 * k];
+    double J = (p[2] - p[0]) * (p[5] - p[1]) - (p[4] - p[0]) * (p[3] - p[1]);
+    double l2 = std::max({(p[2] - p[0]) * (p[2] - p[0]) + (p[3] - p[1]) * (p[3] - p[1]),
+                          (p[4] - p[2]) * (p[4] - p[2]) + (p[5] - p[3]) * (p[5] - p[3]),
+                          (p[0] - p[4]) * (p[0] - p[4]) + (p[1] - p[5]) * (p[1] - p[5])});
+    if (!(J > 1e-12 * l2)) return fail(ctx, RDG_EMESH, "triangle " + std::to_string(k) + " is clockwise or degenerate");
+    hmin = std::min(hmin, std::sqrt(l2));
+  }
+  (void)hmin;
+  // match faces by their midpoint (modulo the period)
+  struct Key {
+    long long x, y;
+    bool operator==(const Key& o) const { return x == o.x && y == o.y; }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const { return std::hash<long long>()(k.x * 1000003LL ^ k.y); }
+  };
+  const double scale = (bc == RDG_BC_PERIODIC) ? 1e9 : 1e12;
+  auto canon = [&](double x, double y) {
+    if (bc == RDG_BC_PERIODIC) {
+      x = std::fmod(x, period[0]);
+      if (x < 0) x += period[0];
+      if (std::fabs(x - period[0]) < 1e-9) x = 0;
+      y = std::fmod(y, period[1]);
+      if (y < 0) y += period[1];
+      if (std::fabs(y - period[1]) < 1e-9) y = 0;
+    }
+    return Key{std::llround(x * scale), std::llround(y * scale)};
+  };
+  std::unordered_map<Key, std::vector<int64_t>, KeyHash> table;
+  table.reserve(nt * 2);
+  for (int64_t k = 0; k < nt; ++k)
+    for (int f = 0; f < 3; ++f) {
+      const double* p = &ctx->exy[6 * k];
+      double mx = 0.5 * (p[2 * kFaceA[f]] + p[2 * kFaceB[f]]), my = 0.5 * (p[2 * kFaceA[f] + 1] + p[2 * kFaceB[f] + 1]);
+      table[canon(mx, my)].push_back(3 * k + f);
+    }
+  std::vector<EdgeRec> inner, bnd;
+  inner.reserve(table.size());
+  for (auto& kv : table) {
+    auto& l = kv.second;
+    if (l.size() > 2) return fail(ctx, RDG_EMESH, "non-manifold edge (shared by more than two faces)");
+    if (l.size() == 2) {
+      int64_t a = std::min(l[0], l[1]), b = std::max(l[0], l[1]);
+      EdgeRec r;
+      r.k1 = (int32_t)(a / 3);
+      r.f1 = (int32_t)(a % 3);
+      r.k2 = (int32_t)(b / 3);
+      r.f2 = (int32_t)(b % 3);
+      const double* p1 = &ctx->exy[6 * r.k1];
+      const double* p2 = &ctx->exy[6 * r.k2];
+      // the two faces must run in opposite directions over the same segment
+      double ax = p1[2 * kFaceA[r.f1]], ay = p1[2 * kFaceA[r.f1] + 1];
+      double bx = p1[2 * kFaceB[r.f1]], by = p1[2 * kFaceB[r.f1] + 1];
+      double cx = p2[2 * kFaceA[r.f2]], cy = p2[2 * kFaceA[r.f2] + 1];
+      double dx = p2[2 * kFaceB[r.f2]], dy = p2[2 * kFaceB[r.f2] + 1];
+      r.shx = 0.5 * (ax + bx) - 0.5 * (cx + dx);
+      r.shy = 0.5 * (ay + by) - 0.5 * (cy + dy);
+      double tol = 1e-9 * std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+      if (std::fabs(dx + r.shx - ax) > tol || std::fabs(dy + r.shy - ay) > tol ||
+          std::fabs(cx + r.shx - bx) > tol || std::fabs(cy + r.shy - by) > tol)
+        return fail(ctx, RDG_EMESH, "faces meeting at an edge midpoint do not coincide");
+      inner.push_back(r);
+    } else {
+      if (bc == RDG_BC_PERIODIC) return fail(ctx, RDG_EMESH, "unmatched face on a periodic mesh");
+      EdgeRec r{(int32_t)(l[0] / 3), (int32_t)(l[0] % 3), -1, 1, 0.0, 0.0};
+      bnd.push_back(r);
+    }
+  }
+  // edges sorted by their first element for locality of the neighbour gathers
+  auto less = [](const EdgeRec& a, const EdgeRec& b) { return a.k1 != b.k1 ? a.k1 < b.k1 : a.f1 < b.f1; };
+  std::sort(inner.begin(), inner.end(), less);
+  std::sort(bnd.begin(), bnd.end(), less);
+  for (size_t b = 0; b < bnd.size(); ++b) bnd[b].k2 = -1 - (int32_t)b;
+  ctx->edges = inner;
+  ctx->edges.insert(ctx->edges.end(), bnd.begin(), bnd.end());
+  ctx->E = (int64_t)ctx->edges.size();
+  ctx->B = (int64_t)bnd.size();
+  ctx->eref.assign(3 * nt, -1);
+  for (int64_t e = 0; e < ctx->E; ++e) {
+    const EdgeRec& r = ctx->edges[e];
+    ctx->eref[(int64_t)r.f1 * nt + r.k1] = (int32_t)(2 * e);
+    if (r.k2 >= 0) ctx->eref[(int64_t)r.f2 * nt + r.k2] = (int32_t)(2 * e + 1);
+  }
+  for (int64_t i = 0; i < 3 * nt; ++i)
+    if (ctx->eref[i] < 0) return fail(ctx, RDG_EMESH, "a face has no edge");
+  if (2 * ctx->E > (int64_t)INT32_MAX) return fail(ctx, RDG_EINVAL, "too many edges");
+  ctx->mesh_ok = true;
+  return RDG_OK;
+}
+
+int rdg_mesh_counts(const rdg_ctx* ctx, int64_t* nt, int64_t* n_edges, int64_t* n_boundary) {
+  if (!ctx || !ctx->mesh_ok) return RDG_ESTATE;
+  if (nt) *nt = ctx->K;
+  if (n_edges) *n_edges = ctx->E;
+  if (n_boundary) *n_boundary = ctx->B;
+  return RDG_OK;
+}
+
+int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int precision, int nsrc, int nghost,
+                    int64_t* bytes) {
+  if (!bytes || N < 1 || N > kMaxN || nt < 0 || n_edges < 0 || n_boundary < 0) return RDG_EINVAL;
+  if (precision != RDG_FP32 && precision != RDG_FP64) return RDG_EINVAL;
+  const int64_t esz = precision == RDG_FP64 ? 8 : 4;
+  const int64_t Np = np_of(N), Nfp = nfp_of(N);
+  int64_t b = w_bytes(N, n_edges, (int)esz);
+  b += 2 * 4 * n_edges + 3 * 4 * nt;          // k1, k2, eref
+  b += 6 * esz * nt;                           // element coefficients
+  b += n_edges * Nfp * esz;                    // edge fluxes
+  b += 3 * nt * Np * esz;                      // state + two stage buffers
+  b += (int64_t)nsrc * nt * Np * esz + (int64_t)nghost * n_boundary * Np * esz;
+  *bytes = b;
+  return RDG_OK;
+}
+
+}  // extern "C"
+
+static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz, double* W_dense) {
+  const int64_t K = ctx->K, E = ctx->E;
+  std::vector<int32_t> k1(E), f1(E), k2(E), f2(E);
+  std::vector<double> sh(2 * E);
+  for (int64_t e = 0; e < E; ++e) {
+    k1[e] = ctx->edges[e].k1;
+    f1[e] = ctx->edges[e].f1;
+    k2[e] = ctx->edges[e].k2;
+    f2[e] = ctx->edges[e].f2;
+    sh[2 * e] = ctx->edges[e].shx;
+    sh[2 * e + 1] = ctx->edges[e].shy;
+  }
+  std::vector<double> refs = pack_setup_refs(*o);
+  double *d_xy = nullptr, *d_sh = nullptr, *d_D = nullptr, *d_refs = nullptr;
+  int32_t *d_i = nullptr;
+  int rc = RDG_OK;
+  cudaError_t e;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    dfree(d_xy);
+    dfree(d_sh);
+    dfree(d_D);
+    dfree(d_refs);
+    dfree(d_i);
+  };
+  if ((e = cudaMalloc(&d_xy, K * 6 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_sh, 2 * E * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_D, K * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_refs, refs.size() * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_i, 4 * E * sizeof(int32_t))) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(ctx, e, "setup buffers");
+  }
+  cudaStream_t s = ctx->stream;
+  if ((e = cudaMemcpyAsync(d_xy, ctx->exy.data(), K * 6 * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_sh, sh.data(), 2 * E * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_D, ctx->Dk.data(), K * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_refs, refs.data(), refs.size() * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_i, k1.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_i + E, f1.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_i + 2 * E, k2.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_i + 3 * E, f2.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(ctx, e, "setup upload");
+  }
+  if (W_tiled) {
+    if ((e = cudaMemsetAsync(W_tiled, 0, w_bytes(ctx->N, E, esz), s)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(ctx, e, "W clear");
+    }
+  }
+  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy};
+  rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, s);
+  if (rc == RDG_OK && ctx->d_geo && !W_dense)
+    rc = setup_elements(K, d_xy, d_D, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
+  e = cudaStreamSynchronize(s);
+  cleanup();
+  if (rc != RDG_OK) return fail(ctx, rc, "setup kernel launch failed");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "setup kernels");
+  return RDG_OK;
+}
+
+extern "C" {
+
+int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->mesh_ok) return fail(ctx, RDG_ESTATE, "rdg_mesh_upload must come first");
+  if (N < 1 || N > kMaxN) return fail(ctx, RDG_EINVAL, "order N must be in 1..6");
+  if (precision != RDG_FP32 && precision != RDG_FP64) return fail(ctx, RDG_EINVAL, "precision must be FP32 or FP64");
+  if (!D_elem) return fail(ctx, RDG_EINVAL, "D_elem is NULL");
+  if (!std::isfinite(vx) || !std::isfinite(vy)) return fail(ctx, RDG_EINVAL, "velocity not finite");
+  for (int64_t k = 0; k < ctx->K; ++k)
+    if (!(D_elem[k] > 0) || !std::isfinite(D_elem[k])) return fail(ctx, RDG_EINVAL, "D must be positive and finite");
+  const char* msg = "";
+  const RefOps* o = get_refops(N, &msg);
+  if (!o) return fail(ctx, RDG_ERANK, msg);
+  DeviceGuard g(ctx->device);
+  free_ops(ctx);
+  ctx->N = N;
+  ctx->prec = precision;
+  ctx->esz = precision == RDG_FP64 ? 8 : 4;
+  ctx->vx = vx;
+  ctx->vy = vy;
+  ctx->Dk.assign(D_elem, D_elem + ctx->K);
+  const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
+  const int64_t stb = K * Np * esz;
+  CK(cudaMalloc(&ctx->d_W, w_bytes(N, E, (int)esz)));
+  CK(cudaMalloc(&ctx->d_k1, E * 4));
+  CK(cudaMalloc(&ctx->d_k2, E * 4));
+  CK(cudaMalloc(&ctx->d_eref, 3 * K * 4));
+  CK(cudaMalloc(&ctx->d_geo, 6 * K * esz));
+  CK(cudaMalloc(&ctx->d_flux, E * Nfp * esz));
+  CK(cudaMalloc(&ctx->d_u, stb));
+  CK(cudaMalloc(&ctx->d_u1, stb));
+  CK(cudaMalloc(&ctx->d_u2, stb));
+  std::vector<int32_t> k1(E), k2(E);
+  for (int64_t e = 0; e < E; ++e) {
+    k1[e] = ctx->edges[e].k1;
+    k2[e] = ctx->edges[e].k2;
+  }
+  CK(cudaMemcpyAsync(ctx->d_k1, k1.data(), E * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_k2, k2.data(), E * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_eref, ctx->eref.data(), 3 * K * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_u, 0, stb, ctx->stream));
+  int rc = build_edge_ops(ctx, o, ctx->d_W, (int)esz, nullptr);
+  if (rc != RDG_OK) {
+    free_ops(ctx);
+    return rc;
+  }
+  ctx->ops_ok = true;
+  return RDG_OK;
+}
+
+int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  DeviceGuard g(ctx->device);
+  const RefOps* o = get_refops(ctx->N, nullptr);
+  const int64_t nw = (int64_t)o->Nfp * 2 * o->Np * ctx->E;
+  if (W) {
+    double* d = nullptr;
+    CK(cudaMalloc(&d, nw * sizeof(double)));
+    int rc = build_edge_ops(ctx, o, nullptr, 8, d);
+    if (rc == RDG_OK) {
+      cudaError_t e = cudaMemcpy(W, d, nw * sizeof(double), cudaMemcpyDeviceToHost);
+      cudaFree(d);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "copy W");
+    } else {
+      cudaFree(d);
+      return rc;
+    }
+  }
+  if (ids)
+    for (int64_t e = 0; e < ctx->E; ++e) {
+      ids[4 * e] = ctx->edges[e].k1;
+      ids[4 * e + 1] = ctx->edges[e].f1;
+      ids[4 * e + 2] = ctx->edges[e].k2;
+      ids[4 * e + 3] = ctx->edges[e].f2;
+    }
+  return RDG_OK;
+}
+
+int rdg_get_node_coords(rdg_ctx* ctx, double* xy) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!xy) return fail(ctx, RDG_EINVAL, "xy is NULL");
+  const RefOps* o = get_refops(ctx->N, nullptr);
+  for (int64_t k = 0; k < ctx->K; ++k) {
+    const double* p = &ctx->exy[6 * k];
+    for (int i = 0; i < o->Np; ++i) {
+      double r = o->r[i], s = o->s[i];
+      double a = -(r + s) / 2, b = (r + 1) / 2, c = (s + 1) / 2;
+      xy[(k * o->Np + i) * 2] = a * p[0] + b * p[2] + c * p[4];
+      xy[(k * o->Np + i) * 2 + 1] = a * p[1] + b * p[3] + c * p[5];
+    }
+  }
+  return RDG_OK;
+}
+
+int rdg_get_ghost_coords(rdg_ctx* ctx, double* xy) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!xy && ctx->B) return fail(ctx, RDG_EINVAL, "xy is NULL");
+  const RefOps* o = get_refops(ctx->N, nullptr);
+  const int kc[3] = {2, 0, 1};
+  for (int64_t b = 0; b < ctx->B; ++b) {
+    const EdgeRec& r = ctx->edges[ctx->E - ctx->B + b];
+    const double* p = &ctx->exy[6 * r.k1];
+    double e1x = p[2 * kFaceA[r.f1]], e1y = p[2 * kFaceA[r.f1] + 1];
+    double e2x = p[2 * kFaceB[r.f1]], e2y = p[2 * kFaceB[r.f1] + 1];
+    double qx = p[2 * kc[r.f1]], qy = p[2 * kc[r.f1] + 1];
+    // ghost vertices: v1 = reflected apex, v2 = e2, v3 = e1
+    double g[6] = {e1x + e2x - qx, e1y + e2y - qy, e2x, e2y, e1x, e1y};
+    for (int i = 0; i < o->Np; ++i) {
+      double rr = o->r[i], ss = o->s[i];
+      double a = -(rr + ss) / 2, bb = (rr + 1) / 2, c = (ss + 1) / 2;
+      xy[(b * o->Np + i) * 2] = a * g[0] + bb * g[2] + c * g[4];
+      xy[(b * o->Np + i) * 2 + 1] = a * g[1] + bb * g[3] + c * g[5];
+    }
+  }
+  return RDG_OK;
+}
+
+}  // extern "C"
+
+static int upload_converted(rdg_ctx* ctx, void** dst, const double* src, int64_t n) {
+  dfree(*dst);
+  if (n == 0) return RDG_OK;
+  CK(cudaMalloc(dst, n * ctx->esz));
+  if (ctx->esz == 8) {
+    CK(cudaMemcpy(*dst, src, n * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(src, src + n);
+    CK(cudaMemcpy(*dst, f.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  return RDG_OK;
+}
+
+extern "C" {
+
+int rdg_set_forcing(rdg_ctx* ctx, int nsrc, const double* S, const int32_t* src_kind, const double* src_omega,
+                    int nghost, const double* G, const int32_t* ghost_kind, const double* ghost_omega) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (nsrc < 0 || nsrc > RDG_MAX_FORCING_TERMS || nghost < 0 || nghost > RDG_MAX_FORCING_TERMS)
+    return fail(ctx, RDG_EINVAL, "at most 4 source and 4 ghost terms");
+  if ((nsrc && (!S || !src_kind || !src_omega)) || (nghost && (!G || !ghost_kind || !ghost_omega)))
+    return fail(ctx, RDG_EINVAL, "NULL forcing array");
+  if (nghost && ctx->B == 0) return fail(ctx, RDG_EINVAL, "ghost data given but the mesh has no boundary edges");
+  for (int m = 0; m < nsrc; ++m)
+    if (src_kind[m] < 0 || src_kind[m] > 2) return fail(ctx, RDG_EINVAL, "bad source kind");
+  for (int m = 0; m < nghost; ++m)
+    if (ghost_kind[m] < 0 || ghost_kind[m] > 2) return fail(ctx, RDG_EINVAL, "bad ghost kind");
+  DeviceGuard g(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int64_t Np = np_of(ctx->N);
+  int rc = upload_converted(ctx, &ctx->d_S, S, (int64_t)nsrc * ctx->K * Np);
+  if (rc != RDG_OK) return rc;
+  rc = upload_converted(ctx, &ctx->d_G, G, (int64_t)nghost * ctx->B * Np);
+  if (rc != RDG_OK) return rc;
+  Forcing f;
+  f.nsrc = nsrc;
+  f.nghost = nghost;
+  for (int m = 0; m < nsrc; ++m) {
+    f.kind[m] = src_kind[m];
+    f.omega[m] = src_omega[m];
+  }
+  for (int m = 0; m < nghost; ++m) {
+    f.gkind[m] = ghost_kind[m];
+    f.gomega[m] = ghost_omega[m];
+  }
+  ctx->frc = f;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  return RDG_OK;
+}
+
+int rdg_set_state(rdg_ctx* ctx, const void* u, int on_device) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!u) return fail(ctx, RDG_EINVAL, "u is NULL");
+  DeviceGuard g(ctx->device);
+  const int64_t bytes = ctx->K * np_of(ctx->N) * ctx->esz;
+  CK(cudaMemcpyAsync(ctx->d_u, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+  return RDG_OK;
+}
+
+int rdg_get_state(rdg_ctx* ctx, void* out, int to_device) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!out) return fail(ctx, RDG_EINVAL, "out is NULL");
+  DeviceGuard g(ctx->device);
+  const int64_t bytes = ctx->K * np_of(ctx->N) * ctx->esz;
+  CK(cudaMemcpyAsync(out, ctx->d_u, bytes, to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  if (!to_device) CK(cudaStreamSynchronize(ctx->stream));
+  return RDG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// stream kernels go to: the capture stream while a graph is being recorded
+cudaStream_t ls(const rdg_ctx* ctx) { return ctx->capturing ? ctx->cap_stream : ctx->stream; }
+
+template <typename T>
+int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta) {
+  EdgeArgs<T> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const T*)us, (T*)ctx->d_flux, (const T*)ctx->d_G,
+                 ctx->E, ctx->B, ctx->frc, ta};
+  ElemArgs<T> la{(const T*)us, (const T*)un, (T*)out, (const T*)ctx->d_flux, ctx->d_eref, (const T*)ctx->d_geo,
+                 (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta};
+  const bool prof = ctx->prof && !ctx->capturing;
+  cudaStream_t st = ls(ctx);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (prof)
+    for (auto& e : ev) e = take_event(ctx);
+  int rc;
+  if (prof) cudaEventRecord(ev[0], st);
+  if constexpr (sizeof(T) == 4) rc = launch_edge32(ctx->N, ea, st);
+  else rc = launch_edge64(ctx->N, ea, st);
+  if (prof) {
+    cudaEventRecord(ev[1], st);
+    cudaEventRecord(ev[2], st);
+  }
+  if (rc == RDG_OK) {
+    if constexpr (sizeof(T) == 4) rc = launch_elem32(ctx->N, mode, la, st);
+    else rc = launch_elem64(ctx->N, mode, la, st);
+  }
+  if (prof) {
+    cudaEventRecord(ev[3], st);
+    ctx->ev_pending[0].push_back({ev[0], ev[1]});
+    ctx->ev_pending[1].push_back({ev[2], ev[3]});
+  }
+  return rc;
+}
+
+int enqueue_rk_step(rdg_ctx* ctx, const TimeArg& base, double dt) {
+  // stage times t, t + dt, t + dt/2 (as offsets in units of dt)
+  TimeArg t1 = base, t2 = base, t3 = base;
+  t2.off = base.off + 1.0;
+  t3.off = base.off + 0.5;
+  int rc;
+  if (ctx->esz == 4) {
+    float d = (float)dt;
+    rc = enqueue_stage<float>(ctx, ctx->d_u, nullptr, ctx->d_u1, 1, d, t1);
+    if (rc == RDG_OK) rc = enqueue_stage<float>(ctx, ctx->d_u1, ctx->d_u, ctx->d_u2, 2, d, t2);
+    if (rc == RDG_OK) rc = enqueue_stage<float>(ctx, ctx->d_u2, ctx->d_u, ctx->d_u, 3, d, t3);
+  } else {
+    rc = enqueue_stage<double>(ctx, ctx->d_u, nullptr, ctx->d_u1, 1, dt, t1);
+    if (rc == RDG_OK) rc = enqueue_stage<double>(ctx, ctx->d_u1, ctx->d_u, ctx->d_u2, 2, dt, t2);
+    if (rc == RDG_OK) rc = enqueue_stage<double>(ctx, ctx->d_u2, ctx->d_u, ctx->d_u, 3, dt, t3);
+  }
+  return rc;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!u_dev || !rhs_dev) return fail(ctx, RDG_EINVAL, "NULL device array");
+  if (!aligned16(u_dev) || !aligned16(rhs_dev)) return fail(ctx, RDG_EINVAL, "device arrays must be 16-byte aligned");
+  if (u_dev == rhs_dev) return fail(ctx, RDG_EINVAL, "u and rhs must not overlap");
+  DeviceGuard g(ctx->device);
+  TimeArg ta{nullptr, t, 1.0, 0.0};
+  int rc = ctx->esz == 4 ? enqueue_stage<float>(ctx, u_dev, nullptr, rhs_dev, 0, 0.0f, ta)
+                         : enqueue_stage<double>(ctx, u_dev, nullptr, rhs_dev, 0, 0.0, ta);
+  return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_rk_step(rdg_ctx* ctx, double t, double dt) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!(dt > 0) || !std::isfinite(t)) return fail(ctx, RDG_EINVAL, "dt must be positive and t finite");
+  DeviceGuard g(ctx->device);
+  TimeArg ta{nullptr, t, dt, 0.0};
+  int rc = enqueue_rk_step(ctx, ta, dt);
+  return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!(dt > 0) || !std::isfinite(t0) || nsteps < 0) return fail(ctx, RDG_EINVAL, "bad t0, dt or nsteps");
+  if (nsteps == 0) return RDG_OK;
+  DeviceGuard g(ctx->device);
+  const int chunk = ctx->prof ? (int)(nsteps + 1) : 16;   // profiling steps without the graph
+  if (nsteps >= chunk && (!ctx->gexec || ctx->g_dt != dt)) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    cudaGraph_t graph;
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    int rc = RDG_OK;
+    for (int i = 0; i < chunk && rc == RDG_OK; ++i) {
+      // the captured steps read their time origin and step count from device memory
+      TimeArg ta{ctx->d_time, 0.0, dt, (double)i};
+      rc = enqueue_rk_step(ctx, ta, dt);
+    }
+    if (rc == RDG_OK) rc = advance_time(ctx->d_time, chunk, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->capturing = false;
+    if (rc != RDG_OK) return fail(ctx, rc, "capture failed");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->g_dt = dt;
+    ctx->g_chunk = chunk;
+  }
+  int64_t done = 0;
+  if (nsteps >= chunk) {
+    int rc = set_time(ctx->d_time, t0, ctx->stream);
+    if (rc != RDG_OK) return fail(ctx, rc, "kernel launch failed");
+    for (; done + chunk <= nsteps; done += chunk) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  }
+  for (; done < nsteps; ++done) {
+    TimeArg ta{nullptr, t0 + done * dt, dt, 0.0};
+    int rc = enqueue_rk_step(ctx, ta, dt);
+    if (rc != RDG_OK) return fail(ctx, rc, "kernel launch failed");
+  }
+  return RDG_OK;
+}
+
+int rdg_profile(rdg_ctx* ctx, int enable) {
+  if (!ctx) return RDG_EINVAL;
+  ctx->prof = enable != 0;
+  return RDG_OK;
+}
+
+int rdg_kernel_stats(rdg_ctx* ctx, int64_t* launches, double* ms, int reset) {
+  if (!ctx) return RDG_EINVAL;
+  DeviceGuard g(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  drain_events(ctx);
+  for (int c = 0; c < 2; ++c) {
+    if (launches) launches[c] = ctx->prof_n[c];
+    if (ms) ms[c] = ctx->prof_ms[c];
+    if (reset) {
+      ctx->prof_n[c] = 0;
+      ctx->prof_ms[c] = 0;
+    }
+  }
+  return RDG_OK;
+}
+
+int rdg_synchronize(rdg_ctx* ctx) {
+  if (!ctx) return RDG_EINVAL;
+  DeviceGuard g(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  return RDG_OK;
+}
+
+int rdg_reference_operator(int N, int which, double* out) {
+  if (!out) return RDG_EINVAL;
+  const char* msg = "";
+  const RefOps* o = get_refops(N, &msg);
+  if (!o) return RDG_EINVAL;
+  const std::vector<double>* src = nullptr;
+  switch (which) {
+    case 0:
+      std::copy(o->r.begin(), o->r.end(), out);
+      std::copy(o->s.begin(), o->s.end(), out + o->Np);
+      return RDG_OK;
+    case 1: src = &o->Dr; break;
+    case 2: src = &o->Ds; break;
+    case 3: src = &o->LIFT; break;
+    case 4: src = &o->Apinv; break;
+    case 5: src = &o->M; break;
+    default: return RDG_EINVAL;
+  }
+  std::copy(src->begin(), src->end(), out);
+  return RDG_OK;
+}
+
+}  // extern "C"

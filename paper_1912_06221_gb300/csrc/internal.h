@@ -1,0 +1,100 @@
+// Internal declarations shared by the host code and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rdg.h"
+#include "refops.h"
+
+namespace rdg {
+
+constexpr int kTile = 32;            // edges per W tile (one warp, one edge per lane)
+constexpr int kElemBlock = 128;      // elements per element-kernel block
+constexpr int kEdgeBlock = 128;      // edges per edge-kernel block
+
+// Words (of 16 bytes) per edge row block of the tiled flux operator.
+inline int w_vecs_per_edge(int N, int elem_bytes) {
+  int nw = nfp_of(N) * 2 * np_of(N);
+  int per = 16 / elem_bytes;
+  return (nw + per - 1) / per;
+}
+
+struct Forcing {
+  int nsrc = 0, nghost = 0;
+  int kind[RDG_MAX_FORCING_TERMS] = {0}, gkind[RDG_MAX_FORCING_TERMS] = {0};
+  double omega[RDG_MAX_FORCING_TERMS] = {0}, gomega[RDG_MAX_FORCING_TERMS] = {0};
+};
+
+// Device-resident time origin of a captured graph: step n of the replay starts at t0 + n dt.
+struct TimeState {
+  double t0;
+  long long n;
+};
+
+// Stage time: ts ? ts->t0 + (ts->n + off) dt : t0 + off dt
+struct TimeArg {
+  const TimeState* ts;
+  double t0, dt, off;
+};
+
+template <typename T>
+struct EdgeArgs {
+  const int32_t* k1;
+  const int32_t* k2;   // >= 0 element, or -1-b for boundary edge b (ghost data)
+  const void* W;       // tiled operator
+  const T* u;
+  T* flux;             // [E][Nfp]
+  const T* G;          // [nghost][B][Np]
+  int64_t E, B;
+  Forcing frc;
+  TimeArg time;
+};
+
+template <typename T>
+struct ElemArgs {
+  const T* us;         // stage input
+  const T* un;         // step start (RK combination)
+  T* out;
+  const T* flux;
+  const int32_t* eref; // [3][K]: 2*edge + (1 if the element is side 2)
+  const T* geo;        // [6][K]: a_r, a_s, g_rr, g_rs, g_ss, 1/J
+  const T* S;          // [nsrc][K][Np]
+  int64_t K;
+  T dt;
+  Forcing frc;
+  TimeArg time;
+};
+
+// mode: 0 rhs only; 1..3 the three SSP-RK3 stage combinations
+int launch_edge32(int N, const EdgeArgs<float>& a, cudaStream_t s);
+int launch_edge64(int N, const EdgeArgs<double>& a, cudaStream_t s);
+int launch_elem32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s);
+int launch_elem64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s);
+int upload_elem_tables(int device);
+
+// ---- setup (FP64) -------------------------------------------------------------------
+struct EdgeSetupIn {
+  const double* xy;        // [K][6] element vertex coordinates
+  const int32_t* k1;
+  const int32_t* f1;
+  const int32_t* k2;       // -1-b for boundary edge b
+  const int32_t* f2;
+  const double* shift;     // [E][2]
+  const double* D;         // [K]
+  const double* refs;      // per-order reference constants (layout in setup.cu)
+  int64_t E;
+  double vx, vy;
+};
+
+int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s);
+int setup_elements(int64_t K, const double* xy, const double* D, double vx, double vy, void* geo, int elem_bytes,
+                   cudaStream_t s);
+// Reference constants for the setup kernel, flattened in the order setup.cu reads them.
+std::vector<double> pack_setup_refs(const RefOps& o);
+int advance_time(TimeState* ts, long long by, cudaStream_t s);
+int set_time(TimeState* ts, double t0, cudaStream_t s);
+
+}  // namespace rdg

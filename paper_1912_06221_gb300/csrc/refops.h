@@ -1,0 +1,46 @@
+// Host FP64 reference-element operators of the aRDG method, one set per order N = 1..6.
+// All of these are constants of the reference triangle / logical square, computed once per
+// order and copied to the device.
+#pragma once
+#include <vector>
+
+#ifdef __CUDACC__
+#define RDG_HD __host__ __device__
+#else
+#define RDG_HD
+#endif
+
+namespace rdg {
+
+constexpr int kMaxN = 6;
+RDG_HD constexpr int np_of(int N) { return (N + 1) * (N + 2) / 2; }
+RDG_HD constexpr int nfp_of(int N) { return N + 1; }
+RDG_HD constexpr int mp_of(int N) { return (N + 1) * (N + 1); }
+
+struct RefOps {
+  int N = 0, Np = 0, Nfp = 0, Mp = 0;
+  std::vector<double> r, s;          // nodes [Np]
+  std::vector<double> V, Vinv;       // Vandermonde (orthonormal basis) [Np][Np], row = node
+  std::vector<double> M;             // mass matrix [Np][Np]
+  std::vector<double> Dr, Ds;        // differentiation [Np][Np]
+  std::vector<double> Wr, Ws;        // weak derivatives M^{-1} Dr^T M, M^{-1} Ds^T M
+  std::vector<double> LIFT;          // [Np][3*Nfp]: column f*Nfp+q
+  std::vector<int> Fmask;            // [3][Nfp] face nodes, counter-clockwise
+  std::vector<int> perm;             // [3][Np]: rotated node i of face f sits at node perm[f][i]
+  std::vector<double> Apinv;         // [Mp][2Np] pseudo-inverse of the reconstruction system
+  double A_cond = 0;                 // smallest/largest |R_ii| of its QR factor
+  // per side k = 0,1: (DR A+)_k Vinv and (DS A+)_k Vinv, [Nfp][Np] each
+  std::vector<double> QRV[2], QSV[2];
+  // Algorithm 2 for element-constant D: D~(diagonal node i) = D1 dvec[0][i] + D2 dvec[1][i],
+  // the reconstruction of the two constants through the same least-squares operator
+  std::vector<double> dvec[2];
+};
+
+// Builds (and caches) the operators of order N; returns nullptr if N is out of range or the
+// reconstruction system is rank deficient (err receives a message).
+const RefOps* get_refops(int N, const char** err);
+
+// Orthonormal basis on the reference triangle at (r, s): psi[Np]; optionally gradients.
+void simplex_basis(int N, double r, double s, double* psi, double* dpsi_dr, double* dpsi_ds);
+
+}  // namespace rdg

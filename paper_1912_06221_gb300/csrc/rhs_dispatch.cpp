@@ -1,0 +1,45 @@
+// Dispatch of the per-order kernel objects by order and precision.
+#include "internal.h"
+
+namespace rdg {
+
+#define RDG_DECL(tag, T, n)                                                  \
+  int upload_tab_##tag##n();                                                 \
+  int launch_edge_##tag##n(const EdgeArgs<T>& a, cudaStream_t s);            \
+  int launch_elem_##tag##n(int mode, const ElemArgs<T>& a, cudaStream_t s);
+#define RDG_DECL_ALL(tag, T) \
+  RDG_DECL(tag, T, 1) RDG_DECL(tag, T, 2) RDG_DECL(tag, T, 3) RDG_DECL(tag, T, 4) RDG_DECL(tag, T, 5) RDG_DECL(tag, T, 6)
+RDG_DECL_ALL(f, float)
+RDG_DECL_ALL(d, double)
+
+#define RDG_SWITCH(expr_tag, call)                 \
+  switch (N) {                                     \
+    case 1: return call(expr_tag, 1);              \
+    case 2: return call(expr_tag, 2);              \
+    case 3: return call(expr_tag, 3);              \
+    case 4: return call(expr_tag, 4);              \
+    case 5: return call(expr_tag, 5);              \
+    case 6: return call(expr_tag, 6);              \
+  }                                                \
+  return RDG_EINVAL;
+
+#define CALL_EDGE(tag, n) launch_edge_##tag##n(a, s)
+#define CALL_ELEM(tag, n) launch_elem_##tag##n(mode, a, s)
+
+int launch_edge32(int N, const EdgeArgs<float>& a, cudaStream_t s) { RDG_SWITCH(f, CALL_EDGE) }
+int launch_edge64(int N, const EdgeArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_EDGE) }
+int launch_elem32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s) { RDG_SWITCH(f, CALL_ELEM) }
+int launch_elem64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_ELEM) }
+
+int upload_elem_tables(int device) {
+  (void)device;
+  int (*fns[])() = {upload_tab_f1, upload_tab_f2, upload_tab_f3, upload_tab_f4, upload_tab_f5, upload_tab_f6,
+                    upload_tab_d1, upload_tab_d2, upload_tab_d3, upload_tab_d4, upload_tab_d5, upload_tab_d6};
+  for (auto f : fns) {
+    int rc = f();
+    if (rc != RDG_OK) return rc;
+  }
+  return RDG_OK;
+}
+
+}  // namespace rdg

@@ -1,0 +1,43 @@
+// One order / one precision of the hot-path kernels.  The build compiles this file once per
+// (RDG_ORDER in 1..6, RDG_REAL in {float, double}) so the translation units build in
+// parallel; each object holds its order's reference matrices in its own constant bank.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+#ifndef RDG_ORDER
+#error "RDG_ORDER must be defined"
+#endif
+#ifndef RDG_REAL
+#error "RDG_REAL must be defined"
+#endif
+
+#define RDG_CAT2(a, b) a##b
+#define RDG_CAT(a, b) RDG_CAT2(a, b)
+
+namespace {
+constexpr int kN = RDG_ORDER;
+constexpr int kNp = (kN + 1) * (kN + 2) / 2;
+constexpr int kTabN = 4 * kNp * kNp + 3 * kNp * (kN + 1);
+__constant__ RDG_REAL c_tab[kTabN];
+}  // namespace
+#define RDG_TAB c_tab
+#include "rhs_kernels.cuh"
+
+namespace rdg {
+
+int RDG_CAT(upload_tab_, RDG_CAT(RDG_TAG, RDG_ORDER))() {
+  std::vector<RDG_REAL> t = pack_elem_table<RDG_REAL>(kN);
+  if ((int)t.size() != kTabN) return RDG_EINVAL;
+  return cudaMemcpyToSymbol(c_tab, t.data(), t.size() * sizeof(RDG_REAL)) == cudaSuccess ? RDG_OK : RDG_ECUDA;
+}
+
+int RDG_CAT(launch_edge_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_REAL>& a, cudaStream_t s) {
+  return launch_edge_t<RDG_REAL, kN>(a, s);
+}
+
+int RDG_CAT(launch_elem_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<RDG_REAL>& a, cudaStream_t s) {
+  return launch_elem_t<RDG_REAL, kN>(mode, a, s);
+}
+
+}  // namespace rdg

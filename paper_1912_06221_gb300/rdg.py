@@ -1,0 +1,232 @@
+"""ctypes binding of librdg.so (argument marshalling only; every computation runs in the
+library's sm_103a kernels).  Device memory and streams come from PyTorch.
+
+The low-level functions keep the C names (``rdg_rhs_eval`` ...); :class:`Solver` wraps one
+context.  There is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "librdg.so")
+
+RDG_OK, RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA, RDG_EMESH, RDG_ERANK, RDG_ETIMEOUT, RDG_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+BC_PERIODIC, BC_DIRICHLET = 0, 1
+FP64, FP32 = 0, 1
+TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
+ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
+
+# symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_INT = ctypes.c_int
+SIGNATURES = {
+    "rdg_version": (ctypes.c_char_p, []),
+    "rdg_last_error": (ctypes.c_char_p, [_P]),
+    "rdg_create": (_INT, [ctypes.POINTER(_P), _INT, _P]),
+    "rdg_destroy": (_INT, [_P]),
+    "rdg_mesh_upload": (_INT, [_P, _I64, _P, _I64, _P, _I32, _P]),
+    "rdg_operator_setup": (_INT, [_P, _INT, _P, _D, _D, _INT]),
+    "rdg_set_forcing": (_INT, [_P, _INT, _P, _P, _P, _INT, _P, _P, _P]),
+    "rdg_mesh_counts": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "rdg_get_node_coords": (_INT, [_P, _P]),
+    "rdg_get_ghost_coords": (_INT, [_P, _P]),
+    "rdg_set_state": (_INT, [_P, _P, _INT]),
+    "rdg_get_state": (_INT, [_P, _P, _INT]),
+    "rdg_rhs_eval": (_INT, [_P, _P, _P, _D]),
+    "rdg_rk_step": (_INT, [_P, _D, _D]),
+    "rdg_solve_to_time": (_INT, [_P, _D, _D, _I64]),
+    "rdg_synchronize": (_INT, [_P]),
+    "rdg_profile": (_INT, [_P, _INT]),
+    "rdg_kernel_stats": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), _INT]),
+    "rdg_query_bytes": (_INT, [_INT, _I64, _I64, _I64, _INT, _INT, _INT, ctypes.POINTER(_I64)]),
+    "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
+    "rdg_get_edge_operators": (_INT, [_P, _P, _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librdg.so (raises if it was not built) and declare every C signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("librdg.so not built (%s): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class RdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("rdg error %s (%d): %s" % (ERR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc != RDG_OK:
+        msg = load().rdg_last_error(ctx)
+        raise RdgError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def np_of(N):
+    return (N + 1) * (N + 2) // 2
+
+
+def query_bytes(N, nt, n_edges, n_boundary, precision, nsrc=0, nghost=0):
+    out = _I64(0)
+    _check(load().rdg_query_bytes(N, nt, n_edges, n_boundary, precision, nsrc, nghost, ctypes.byref(out)))
+    return out.value
+
+
+def reference_operator(N, which):
+    Np, Nfp, Mp = np_of(N), N + 1, (N + 1) ** 2
+    shape = {0: (2, Np), 1: (Np, Np), 2: (Np, Np), 3: (Np, 3 * Nfp), 4: (Mp, 2 * Np), 5: (Np, Np)}[which]
+    out = np.zeros(shape)
+    _check(load().rdg_reference_operator(N, which, _ptr(out)))
+    return out
+
+
+class Solver:
+    """One library context: mesh, operators of order N and the resident state."""
+
+    def __init__(self, xy, tri, N: int, D_elem, v=(0.0, 0.0), bc: int = BC_PERIODIC, period=(1.0, 1.0),
+                 precision: int = FP32, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = device
+        self.N, self.Np, self.Nfp = N, np_of(N), N + 1
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.np_dtype = np.float64 if precision == FP64 else np.float32
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        ctx = _P()
+        handle = stream.cuda_stream
+        if handle == 0:
+            handle = 1      # torch's default stream is the legacy default stream (cudaStreamLegacy)
+        _check(self.lib.rdg_create(ctypes.byref(ctx), device, _P(handle)))
+        self.ctx = ctx
+        xy = np.ascontiguousarray(xy, np.float64)
+        tri = np.ascontiguousarray(tri, np.int32)
+        per = np.ascontiguousarray(period if period is not None else (0.0, 0.0), np.float64)
+        self._call("rdg_mesh_upload", xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), bc,
+                   _ptr(per) if period is not None else None)
+        D = np.ascontiguousarray(np.broadcast_to(np.asarray(D_elem, np.float64), (tri.shape[0],)))
+        self._call("rdg_operator_setup", N, _ptr(D), float(v[0]), float(v[1]), precision)
+        K, E, B = _I64(), _I64(), _I64()
+        self._call("rdg_mesh_counts", ctypes.byref(K), ctypes.byref(E), ctypes.byref(B))
+        self.K, self.E, self.B = K.value, E.value, B.value
+
+    def _call(self, name, *args):
+        _check(getattr(self.lib, name)(self.ctx, *args), self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.rdg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- geometry ---------------------------------------------------------------------
+    def node_coords(self):
+        out = np.zeros((self.K, self.Np, 2))
+        self._call("rdg_get_node_coords", _ptr(out))
+        return out
+
+    def ghost_coords(self):
+        out = np.zeros((self.B, self.Np, 2))
+        self._call("rdg_get_ghost_coords", _ptr(out) if self.B else None)
+        return out
+
+    def edge_operators(self):
+        W = np.zeros((self.E, self.Nfp, 2 * self.Np))
+        ids = np.zeros((self.E, 4), np.int32)
+        self._call("rdg_get_edge_operators", _ptr(W), _ptr(ids))
+        return W, ids
+
+    # -- forcing ----------------------------------------------------------------------
+    def set_forcing(self, src: Sequence = (), ghost: Sequence = ()):
+        """src: [(S nodal [K, Np], kind, omega)], ghost: [(G [B, Np] at ghost nodes, kind, omega)]."""
+        S = np.ascontiguousarray(np.stack([np.asarray(s[0], np.float64) for s in src])) if src else None
+        sk = np.array([s[1] for s in src], np.int32)
+        so = np.array([s[2] for s in src], np.float64)
+        G = np.ascontiguousarray(np.stack([np.asarray(g[0], np.float64) for g in ghost])) if ghost else None
+        gk = np.array([g[1] for g in ghost], np.int32)
+        go = np.array([g[2] for g in ghost], np.float64)
+        self._call("rdg_set_forcing", len(src), _ptr(S) if S is not None else None, _ptr(sk), _ptr(so),
+                   len(ghost), _ptr(G) if G is not None else None, _ptr(gk), _ptr(go))
+
+    # -- state and stepping ----------------------------------------------------------
+    def _dev_tensor(self, t):
+        torch = self.torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and t.is_contiguous()
+                and t.numel() == self.K * self.Np):
+            raise ValueError("expected a contiguous CUDA %s tensor of %d values" % (self.dtype, self.K * self.Np))
+        return _P(t.data_ptr())
+
+    def new_field(self):
+        return self.torch.zeros((self.K, self.Np), dtype=self.dtype, device="cuda:%d" % self.device)
+
+    def set_state(self, u):
+        if isinstance(u, np.ndarray):
+            a = np.ascontiguousarray(u, self.np_dtype)
+            self._call("rdg_set_state", _ptr(a), 0)
+        else:
+            self._call("rdg_set_state", self._dev_tensor(u), 1)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = self.new_field()
+        self._call("rdg_get_state", self._dev_tensor(out), 1)
+        return out
+
+    def get_state_host(self):
+        a = np.zeros((self.K, self.Np), self.np_dtype)
+        self._call("rdg_get_state", _ptr(a), 0)
+        return a
+
+    def rhs_eval(self, u, rhs, t: float = 0.0):
+        self._call("rdg_rhs_eval", self._dev_tensor(u), self._dev_tensor(rhs), float(t))
+
+    def rk_step(self, t: float, dt: float):
+        self._call("rdg_rk_step", float(t), float(dt))
+
+    def solve_to_time(self, t0: float, dt: float, nsteps: int):
+        self._call("rdg_solve_to_time", float(t0), float(dt), int(nsteps))
+
+    def synchronize(self):
+        self._call("rdg_synchronize")
+
+    def profile(self, enable: bool = True):
+        self._call("rdg_profile", 1 if enable else 0)
+
+    def kernel_stats(self, reset: bool = True):
+        """{'edge': (launches, ms), 'elem': (launches, ms)} of the event-timed launches."""
+        n = (_I64 * 2)()
+        ms = (_D * 2)()
+        self._call("rdg_kernel_stats", n, ms, 1 if reset else 0)
+        return {"edge": (n[0], ms[0]), "elem": (n[1], ms[1])}

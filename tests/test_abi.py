@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports every symbol include/rdg.h declares (no GPU:
+no compute call is made)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06221_gb300 as rdg
+    return rdg.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rdg_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_binding_declares_every_symbol():
+    from paper_1912_06221_gb300.rdg import SIGNATURES
+    assert declared_symbols() == set(SIGNATURES)
+
+
+def test_host_only_entry_points(lib):
+    import paper_1912_06221_gb300 as rdg
+    assert lib.rdg_version().startswith(b"rdg-gb300")
+    # admission bytes: W operator + indices + coefficients + fluxes + state buffers
+    N, K, E = 4, 131072, 196608
+    b = rdg.query_bytes(N, K, E, 0, rdg.FP32)
+    W = ((E + 31) // 32) * 38 * 32 * 16
+    assert b == W + 8 * E + 12 * K + 24 * K + E * 5 * 4 + 3 * K * 15 * 4
+    assert rdg.query_bytes(N, K, E, 0, rdg.FP64) > b
+    with pytest.raises(rdg.RdgError):
+        rdg.query_bytes(7, K, E, 0, rdg.FP32)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_library_reference_operators_match_oracle(lib, N):
+    """The library's host FP64 reference operators (its own implementation) agree with the
+    oracle's to rounding."""
+    import paper_1912_06221_gb300 as rdg
+    from oracle.refops import RefOps
+    o = RefOps(N)
+    rs = rdg.reference_operator(N, 0)
+    assert np.abs(rs[0] - o.r).max() < 1e-14 and np.abs(rs[1] - o.s).max() < 1e-14
+    sc = (N + 1) ** 2
+    assert np.abs(rdg.reference_operator(N, 1) - o.Dr).max() < 1e-11 * sc
+    assert np.abs(rdg.reference_operator(N, 2) - o.Ds).max() < 1e-11 * sc
+    assert np.abs(rdg.reference_operator(N, 3) - np.concatenate(list(o.LIFT), axis=1)).max() < 1e-12 * sc
+    assert np.abs(rdg.reference_operator(N, 4) - o.Apinv).max() < 1e-12 * sc
+    assert np.abs(rdg.reference_operator(N, 5) - o.M).max() < 1e-14 * sc
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    ctx = ctypes.c_void_p()
+    rc = lib.rdg_create(ctypes.byref(ctx), 0, None)
+    assert rc != 0 and lib.rdg_last_error(None)

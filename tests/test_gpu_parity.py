@@ -1,0 +1,213 @@
+"""GPU parity: the sm_103a library through its C ABI against the FP64 oracle.
+
+Meshes span several kernel tiles with a ragged tail (128-element blocks, 32-edge tiles):
+m = 9 gives 162 triangles and 243 edges.  Tolerances (normwise relative): FP64 <= 1e-12 for
+one right-hand side, <= 1e-10 for a state after many steps; FP32 <= 1e-5 (rounding of
+O(1e-7) per operation accumulated over the few hundred terms of a row, well inside 1e-5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1912_06221_gb300 as rdg
+from synth import unit_square_mesh, random_nodal, PERIODIC, DIRICHLET, heat_sin_mode
+from oracle.mesh import Mesh
+from oracle.rhs import Problem, stable_dt
+
+TOL = {rdg.FP64: 1e-12, rdg.FP32: 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _setup(N, m=9, seed=3, bc=PERIODIC, prec=rdg.FP64, v=(0.7, -0.4), varD=True, jitter=0.1):
+    xy, tri = unit_square_mesh(m, jitter, seed)
+    K = tri.shape[0]
+    D = np.where(np.random.default_rng(seed).uniform(size=K) < 0.3, 1.0, 0.02) if varD else np.full(K, 0.5)
+    s = rdg.Solver(xy, tri, N, D, v=v, bc=bc, precision=prec)
+    me = Mesh(xy, tri, N, bc=bc)
+    return s, me, D
+
+
+GF = [(lambda x, y: np.sin(np.pi * x) * np.cos(2 * np.pi * y), rdg.TAU_COS, 1.0),
+      (lambda x, y: 0.3 * x * y + 0.1, rdg.TAU_SIN, 2.0)]
+SF = [(lambda x, y: np.cos(3 * x) * y, rdg.TAU_CONST, 0.0), (lambda x, y: x - y * y, rdg.TAU_SIN, 5.0)]
+
+
+def _tau(kind, om, t):
+    return 1.0 if kind == rdg.TAU_CONST else (math.cos(om * t) if kind == rdg.TAU_COS else math.sin(om * t))
+
+
+def _forcing(s, me, with_src=True, with_ghost=True):
+    """Install the same separable source/ghost data on both sides (each at its own nodes)."""
+    xyn = s.node_coords()
+    src = [(f(xyn[..., 0], xyn[..., 1]), k, o) for f, k, o in SF] if with_src else []
+    gh = []
+    if with_ghost and s.B:
+        gxy = s.ghost_coords()
+        gh = [(f(gxy[..., 0], gxy[..., 1]), k, o) for f, k, o in GF]
+    s.set_forcing(src, gh)
+    osrc = [(f(me.x, me.y), k, o) for f, k, o in SF] if with_src else []
+    gfn = (lambda x, y, t: sum(f(x, y) * _tau(k, o, t) for f, k, o in GF)) if with_ghost else None
+    return osrc, gfn
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
+def test_node_coords_match_oracle(N, prec):
+    s, me, D = _setup(N, prec=prec)
+    xy = s.node_coords()
+    assert np.abs(xy[..., 0] - me.x).max() < 1e-14 and np.abs(xy[..., 1] - me.y).max() < 1e-14
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("bc", [PERIODIC, DIRICHLET])
+def test_edge_operators_match_oracle(N, bc):
+    """Per-edge FP64 flux operators built on the GPU equal the oracle's composition
+    J_f ( -D~ n1.grad(reconstruction) + upwind ) edge by edge."""
+    s, me, D = _setup(N, bc=bc)
+    W, ids = s.edge_operators()
+    pr = Problem(me, D, v=(0.7, -0.4), ghost_fn=(lambda x, y, t: 0 * x))
+    eo = pr.eops
+    ops = me.ops
+    key = {}
+    for e, (k1, f1, k2, f2, _, _) in enumerate(me.edges):
+        key[(k1, f1)] = e
+    Np, Nfp = ops.Np, ops.Nfp
+    for el in range(s.E):
+        k1, f1, k2, f2 = ids[el]
+        e = key.get((k1, f1))
+        swapped = False
+        if e is None:
+            e = key[(k2, f2)]
+            swapped = True
+        # oracle operator: g = n1.grad u~ as a linear map of [u1; u2]
+        Rx, Ry, Sx, Sy = eo.Rx[e]
+        n1 = eo.n1[e]
+        G = (n1[0] * Rx + n1[1] * Ry) * ops.DR + (n1[0] * Sx + n1[1] * Sy) * ops.DS
+        Op = G @ ops.Apinv @ np.block([[eo.P1[e], np.zeros((Np, Np))], [np.zeros((Np, Np)), eo.P2[e]]])
+        Jf = me.sJ[me.edges[e][0], me.edges[e][1]]
+        Wo = -Jf * pr.Dt[e][:, None] * Op
+        vn = n1 @ pr.v
+        for i in range(Nfp):
+            if vn >= 0:
+                Wo[i, ops.Fmask[me.edges[e][1]][i]] += Jf * vn
+            else:
+                f2o = me.edges[e][3] if me.edges[e][2] >= 0 else 1
+                Wo[i, Np + ops.Fmask[f2o][Nfp - 1 - i]] += Jf * vn
+        if swapped:   # the library took the other element as side 1: flux negated, reversed
+            Wo = -Wo[::-1][:, np.r_[Np:2 * Np, 0:Np]]
+        scale = np.abs(Wo).max()
+        assert np.abs(W[el] - Wo).max() < 1e-11 * scale, (el, np.abs(W[el] - Wo).max() / scale)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
+@pytest.mark.parametrize("bc", [PERIODIC, DIRICHLET])
+def test_rhs_parity(N, prec, bc):
+    s, me, D = _setup(N, prec=prec, bc=bc)
+    osrc, gfn = _forcing(s, me, with_src=True, with_ghost=(bc == DIRICHLET))
+    pr = Problem(me, D, v=(0.7, -0.4), source=osrc, ghost_fn=gfn)
+    u = random_nodal(s.K, s.Np, 11)
+    ud = torch.tensor(u, dtype=s.dtype, device="cuda")
+    rd = torch.empty_like(ud)
+    t = 0.37
+    s.rhs_eval(ud, rd, t)
+    s.synchronize()
+    want = pr.rhs(u.astype(np.float32).astype(np.float64) if prec == rdg.FP32 else u, t)
+    assert relerr(rd.cpu().numpy(), want) < TOL[prec]
+
+
+@pytest.mark.parametrize("N", [2, 4, 6])
+@pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
+def test_rk_steps_and_graph_replay(N, prec):
+    """Direct SSP-RK3 steps and the CUDA-graph replay (a chunk of 16 steps plus a remainder)
+    both follow the oracle, with time-dependent sources and Dirichlet ghosts."""
+    s, me, D = _setup(N, prec=prec, bc=DIRICHLET, m=7)
+    osrc, gfn = _forcing(s, me)
+    pr = Problem(me, D, v=(0.7, -0.4), source=osrc, ghost_fn=gfn)
+    u0 = random_nodal(s.K, s.Np, 5) * 0.1 + me.x
+    if prec == rdg.FP32:
+        u0 = u0.astype(np.float32).astype(np.float64)
+    dt = stable_dt(pr, 0.4, 20)
+    t0 = 0.125
+    s.set_state(u0)
+    for n in range(3):
+        s.rk_step(t0 + n * dt, dt)
+    got = s.get_state_host()
+    want = pr.solve(u0, t0, dt, 3)
+    assert relerr(got, want) < (1e-11 if prec == rdg.FP64 else 1e-5)
+    s.set_state(u0)
+    s.solve_to_time(t0, dt, 21)
+    got = s.get_state_host()
+    want = pr.solve(u0, t0, dt, 21)
+    assert relerr(got, want) < (1e-10 if prec == rdg.FP64 else 2e-5)
+
+
+def test_heat_sin_mode_fp64_full_run():
+    """N = 2, 16x16x2 jittered periodic mesh, 200 steps at dt = 0.1 h^2/(D (N+1)^4): the GPU
+    FP64 state equals the oracle's, and both decay at the exact rate exp(-8 pi^2 D t)."""
+    w = heat_sin_mode()
+    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, precision=rdg.FP64)
+    xyn = s.node_coords()
+    u0 = w.u0(xyn[..., 0], xyn[..., 1])
+    s.set_state(u0)
+    s.solve_to_time(0.0, w.dt, w.steps)
+    got = s.get_state_host()
+    me = Mesh(w.xy, w.tri, w.N)
+    pr = Problem(me, w.D_elem)
+    want = pr.solve(w.u0(me.x, me.y), 0.0, w.dt, w.steps)
+    assert relerr(got, want) < 1e-10
+    T = w.steps * w.dt
+    Mw = me.J[:, None] * (u0 @ me.ops.M)
+    rate = math.log(np.sum(Mw * got) / np.sum(Mw * u0)) / (-8 * math.pi ** 2 * T)
+    assert abs(rate - 1) < 1e-2
+
+
+def test_conservation_and_constants_on_gpu():
+    s, me, D = _setup(4, m=12, prec=rdg.FP64)
+    u = torch.full((s.K, s.Np), 1.75, dtype=torch.float64, device="cuda")
+    r = torch.empty_like(u)
+    s.rhs_eval(u, r, 0.0)
+    s.synchronize()
+    assert float(r.abs().max()) < 1e-9
+    ur = torch.tensor(random_nodal(s.K, s.Np, 2), device="cuda")
+    s.rhs_eval(ur, r, 0.0)
+    s.synchronize()
+    tot = np.sum(me.J[:, None] * (r.cpu().numpy() @ me.ops.M))
+    scale = np.sum(np.abs(me.J[:, None] * (r.cpu().numpy() @ me.ops.M)))
+    assert abs(tot) < 1e-12 * scale
+
+
+def test_error_paths():
+    xy, tri = unit_square_mesh(3, 0.1, 0)
+    bad = tri.copy()
+    bad[0] = bad[0][::-1]          # clockwise triangle
+    with pytest.raises(rdg.RdgError) as ei:
+        rdg.Solver(xy, bad, 2, 1.0)
+    assert ei.value.code == -4
+    with pytest.raises(rdg.RdgError) as ei:
+        rdg.Solver(xy, tri, 7, 1.0)
+    assert ei.value.code == -1
+    with pytest.raises(rdg.RdgError) as ei:
+        rdg.Solver(xy, tri, 2, -1.0)
+    assert ei.value.code == -1
+    # a periodic mesh that is not periodic (Dirichlet-style hole): drop one triangle
+    with pytest.raises(rdg.RdgError) as ei:
+        rdg.Solver(xy, tri[1:], 2, 1.0)
+    assert ei.value.code == -4
+    s = rdg.Solver(xy, tri, 2, 1.0)
+    with pytest.raises(ValueError):
+        s.rhs_eval(torch.zeros(3, device="cuda"), torch.zeros(3, device="cuda"))
