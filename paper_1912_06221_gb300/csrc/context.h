@@ -1,0 +1,55 @@
+// Definition of the library context (shared by the translation units that enqueue work).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+struct EdgeRec {
+  int32_t k1, f1, k2, f2;  // k2 = -1 - b for boundary edge b
+  double shx, shy;
+};
+
+struct rdg_ctx {
+  using Forcing = rdg::Forcing;
+  using TimeState = rdg::TimeState;
+  int device = 0;
+  cudaStream_t stream = nullptr;     // the caller's stream (may be the legacy default stream)
+  cudaStream_t cap_stream = nullptr; // private stream used only to capture graphs
+  bool capturing = false;
+  bool own_stream = false;
+  std::string err;
+  // mesh (host)
+  bool mesh_ok = false;
+  int64_t K = 0, E = 0, B = 0;
+  int bc = 0;
+  std::vector<double> exy;       // [K][6]
+  std::vector<EdgeRec> edges;    // interior edges first, then boundary edges
+  std::vector<int32_t> eref;     // [3][K]
+  // operators
+  bool ops_ok = false;
+  int N = 0, prec = RDG_FP32, esz = 4;
+  double vx = 0, vy = 0;
+  std::vector<double> Dk;
+  // device buffers
+  void* d_W = nullptr;
+  int32_t *d_k1 = nullptr, *d_k2 = nullptr, *d_eref = nullptr;
+  void *d_geo = nullptr, *d_flux = nullptr, *d_u = nullptr, *d_u1 = nullptr, *d_u2 = nullptr;
+  void *d_S = nullptr, *d_G = nullptr;
+  TimeState* d_time = nullptr;
+  Forcing frc;
+  // per-kernel event timing (class 0 edge flux, 1 element update)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[2];
+  double prof_ms[2] = {0, 0};
+  int64_t prof_n[2] = {0, 0};
+  // graph of a chunk of steps for one dt
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = 0;
+  int g_chunk = 0;
+};
+
