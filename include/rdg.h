@@ -125,6 +125,21 @@ int rdg_get_state(rdg_ctx* ctx, void* out, int to_device);
  * not overlap (RDG_EINVAL otherwise). */
 int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
 
+/* Allocation-free rhs = L(u, t), for callers that cannot allocate device memory where they
+ * evaluate the right-hand side (inside another component's CUDA-graph capture, in loops
+ * that must not hit cudaMalloc's implicit synchronisation, or under a pool allocator that
+ * owns all device memory).  It computes the same result as rdg_rhs_eval (same kernels) but
+ * keeps the per-edge fluxes in one static device array compiled into the library, 8 MiB,
+ * held by every GPU that loads the library until the process exits; it calls no allocating
+ * routine.  Meshes needing more than 8 MiB of fluxes (n_edges x Nfp x element size) get
+ * RDG_EINVAL with a message.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress with the device current); make that first call before any
+ * stream capture.  All calls share the array, which keeps the last call's contents (every
+ * flux is rewritten before it is read, so nothing is cleared): calls whose GPU work
+ * overlaps (different streams or devices' contexts sharing a device) race on it.  The paper
+ * has no counterpart to this entry point. */
+int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
+
 /* One SSP-RK3 step of the resident state from time t with step dt (stages at t, t+dt,
  * t+dt/2); enqueued, no host synchronisation. */
 int rdg_rk_step(rdg_ctx* ctx, double t, double dt);

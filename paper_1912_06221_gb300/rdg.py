@@ -41,6 +41,7 @@ SIGNATURES = {
     "rdg_set_state": (_INT, [_P, _P, _INT]),
     "rdg_get_state": (_INT, [_P, _P, _INT]),
     "rdg_rhs_eval": (_INT, [_P, _P, _P, _D]),
+    "rdg_rhs_eval_static": (_INT, [_P, _P, _P, _D]),
     "rdg_rk_step": (_INT, [_P, _D, _D]),
     "rdg_solve_to_time": (_INT, [_P, _D, _D, _I64]),
     "rdg_synchronize": (_INT, [_P]),
