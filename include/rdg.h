@@ -57,6 +57,10 @@ enum {
 enum { RDG_BC_PERIODIC = 0, RDG_BC_DIRICHLET = 1 };
 enum { RDG_FP64 = 0, RDG_FP32 = 1 };
 enum { RDG_TAU_CONST = 0, RDG_TAU_COS = 1, RDG_TAU_SIN = 2 };
+/* Edge diffusion coefficient for element-wise D: the paper's Algorithm 2 (D~ = RDG(D1, D2)
+ * on the diagonal) or the harmonic mean 2 D1 D2 / (D1 + D2) (not in the paper: stable for
+ * high-contrast jumps, where Algorithm 2 gives growing modes). Equal when D1 = D2. */
+enum { RDG_IFACE_ALG2 = 0, RDG_IFACE_HARMONIC = 1 };
 #define RDG_MAX_FORCING_TERMS 4
 
 /* Library version string. */
@@ -88,14 +92,16 @@ int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, cons
                     int32_t bc, const double* period);
 
 /* Operators for order N (1..6) with element-wise diffusion D_elem[nt] (> 0), constant
- * velocity (vx, vy), arithmetic precision RDG_FP64 or RDG_FP32.  Builds, in FP64 on the GPU,
+ * velocity (vx, vy), arithmetic precision RDG_FP64 or RDG_FP32, interface rule
+ * RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC for the edge diffusion coefficient.  Builds, in FP64 on the GPU,
  * the element metric terms and for every edge the enclosed parallelogram (Sec. 4.2), the
  * projections V^{-1} V_p V_rf^{-1} of both sides (Eq. totalProjection), the least-squares
  * reconstruction (Sec. 4.5) and the edge-normal gradient, folded with D~ = RDG(D1, D2)
  * (Algorithm 2), the edge Jacobian J_f and the upwind convective trace into one
  * Nfp x 2Np flux operator per edge, stored in the chosen precision.
  * Errors: RDG_ESTATE (no mesh), RDG_EINVAL, RDG_ERANK, RDG_ENOMEM, RDG_ECUDA. */
-int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision);
+int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision,
+                       int interface_rule);
 
 /* Separable forcing (after rdg_operator_setup).  Source s(x,t) = sum_m S_m(x) tau_m(t) with
  * S given as nodal values S[nsrc][nt][Np] (host, double), tau_m = 1, cos(w t) or sin(w t)
@@ -148,6 +154,11 @@ int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
  * graph of a fixed chunk of steps (captured on first use for a given dt); enqueued. */
 int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps);
 
+/* Cap the grid of the persistent edge-flux kernel at max_ctas CTAs (0 restores one CTA per
+ * SM).  With few CTAs each one streams many operator tiles through its shared-memory ring,
+ * which is how the tests exercise the pipeline's wrap-around on small meshes. */
+int rdg_set_launch_limit(rdg_ctx* ctx, int max_ctas);
+
 /* Per-kernel timing.  With enable != 0 every later edge-flux and element-update kernel launch
  * of ctx is bracketed by CUDA events on the context stream (rdg_solve_to_time then steps
  * without its graph).  rdg_kernel_stats waits for the stream and returns, for kernel class
@@ -156,7 +167,8 @@ int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps);
 int rdg_profile(rdg_ctx* ctx, int enable);
 int rdg_kernel_stats(rdg_ctx* ctx, int64_t* launches, double* ms, int reset);
 
-/* Wait for the context's stream; returns RDG_ECUDA if device work failed. */
+/* Wait for the context's stream; returns RDG_ECUDA if device work failed and RDG_ETIMEOUT
+ * if a kernel's bounded wait on its copy pipeline gave up (the error word is then cleared). */
 int rdg_synchronize(rdg_ctx* ctx);
 
 /* Device bytes a context allocates for order N, nt triangles, n_edges edges (n_boundary of

@@ -31,9 +31,16 @@ from .refops import psi, triangle_quadrature
 
 class Problem:
     """A mesh plus coefficients: D per element, constant velocity v, optional separable
-    source and Dirichlet ghost data (lists of (nodal profile, kind, omega))."""
+    source and Dirichlet ghost data (lists of (nodal profile, kind, omega)).
 
-    def __init__(self, mesh: Mesh, D_elem, v=(0.0, 0.0), source=None, ghost_fn=None):
+    interface: how the edge diffusion coefficient D~ is formed for element-wise D.
+      "alg2"      the paper's Algorithm 2, D~ = RDG(D1, D2) on the diagonal;
+      "harmonic"  2 D1 D2 / (D1 + D2), not in the paper: a stabilised variant for
+                  high-contrast jumps (with "alg2" such jumps give operator eigenvalues with
+                  positive real part).  Both equal D when D1 = D2.
+    """
+
+    def __init__(self, mesh: Mesh, D_elem, v=(0.0, 0.0), source=None, ghost_fn=None, interface="alg2"):
         self.mesh = mesh
         self.eops = EdgeOps(mesh)
         self.D = np.asarray(D_elem, float)
@@ -47,7 +54,13 @@ class Problem:
         self.f2 = np.array([e[3] for e in m.edges])
         self.interior = self.k2 >= 0
         D2 = np.where(self.interior, self.D[np.maximum(self.k2, 0)], self.D[self.k1])
-        self.Dt = self.eops.reconstruct_D(self.D[self.k1], D2)
+        if interface == "alg2":
+            self.Dt = self.eops.reconstruct_D(self.D[self.k1], D2)
+        elif interface == "harmonic":
+            D1 = self.D[self.k1]
+            self.Dt = np.repeat((2 * D1 * D2 / (D1 + D2))[:, None], mesh.ops.Nfp, axis=1)
+        else:
+            raise ValueError(interface)
         self.bnd = np.flatnonzero(~self.interior)
         self.ghost_xy = [m.ghost_nodes(e) for e in self.bnd]
 

@@ -64,6 +64,7 @@ void free_ops(rdg_ctx* ctx) {
   dfree(ctx->d_u2);
   dfree(ctx->d_S);
   dfree(ctx->d_G);
+  dfree(ctx->d_vol);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   ctx->gexec = nullptr;
   ctx->ops_ok = false;
@@ -171,7 +172,11 @@ int rdg_create(rdg_ctx** out, int device, void* cuda_stream) {
     c->own_stream = true;
   }
   e = cudaMalloc(&c->d_time, sizeof(TimeState));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
+    if (c->d_time) cudaFree(c->d_time);
+    if (c->d_err) cudaFree(c->d_err);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return fail(nullptr, RDG_ENOMEM, "device allocation failed");
@@ -187,6 +192,7 @@ int rdg_destroy(rdg_ctx* ctx) {
   free_ops(ctx);
   free_events(ctx);
   dfree(ctx->d_time);
+  dfree(ctx->d_err);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -323,7 +329,7 @@ int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int 
   b += 2 * 4 * n_edges + 3 * 4 * nt;          // k1, k2, eref
   b += 6 * esz * nt;                           // element coefficients
   b += n_edges * Nfp * esz;                    // edge fluxes
-  b += 3 * nt * Np * esz;                      // state + two stage buffers
+  b += 4 * nt * Np * esz;                      // state, two stage buffers, volume terms
   b += (int64_t)nsrc * nt * Np * esz + (int64_t)nghost * n_boundary * Np * esz;
   *bytes = b;
   return RDG_OK;
@@ -382,7 +388,7 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
       return cuda_fail(ctx, e, "W clear");
     }
   }
-  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy};
+  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy, ctx->iface};
   rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, s);
   if (rc == RDG_OK && ctx->d_geo && !W_dense)
     rc = setup_elements(K, d_xy, d_D, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
@@ -395,12 +401,15 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
 
 extern "C" {
 
-int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision) {
+int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision,
+                       int interface_rule) {
   if (!ctx) return RDG_EINVAL;
   if (!ctx->mesh_ok) return fail(ctx, RDG_ESTATE, "rdg_mesh_upload must come first");
   if (N < 1 || N > kMaxN) return fail(ctx, RDG_EINVAL, "order N must be in 1..6");
   if (precision != RDG_FP32 && precision != RDG_FP64) return fail(ctx, RDG_EINVAL, "precision must be FP32 or FP64");
   if (!D_elem) return fail(ctx, RDG_EINVAL, "D_elem is NULL");
+  if (interface_rule != RDG_IFACE_ALG2 && interface_rule != RDG_IFACE_HARMONIC)
+    return fail(ctx, RDG_EINVAL, "interface rule must be RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC");
   if (!std::isfinite(vx) || !std::isfinite(vy)) return fail(ctx, RDG_EINVAL, "velocity not finite");
   for (int64_t k = 0; k < ctx->K; ++k)
     if (!(D_elem[k] > 0) || !std::isfinite(D_elem[k])) return fail(ctx, RDG_EINVAL, "D must be positive and finite");
@@ -414,6 +423,7 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   ctx->esz = precision == RDG_FP64 ? 8 : 4;
   ctx->vx = vx;
   ctx->vy = vy;
+  ctx->iface = interface_rule;
   ctx->Dk.assign(D_elem, D_elem + ctx->K);
   const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
   const int64_t stb = K * Np * esz;
@@ -426,6 +436,7 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   CK(cudaMalloc(&ctx->d_u, stb));
   CK(cudaMalloc(&ctx->d_u1, stb));
   CK(cudaMalloc(&ctx->d_u2, stb));
+  CK(cudaMalloc(&ctx->d_vol, stb));
   std::vector<int32_t> k1(E), k2(E);
   for (int64_t e = 0; e < E; ++e) {
     k1[e] = ctx->edges[e].k1;
@@ -600,9 +611,10 @@ cudaStream_t ls(const rdg_ctx* ctx) { return ctx->capturing ? ctx->cap_stream : 
 template <typename T>
 int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta) {
   EdgeArgs<T> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const T*)us, (T*)ctx->d_flux, (const T*)ctx->d_G,
-                 ctx->E, ctx->B, ctx->frc, ta};
+                 ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, ctx->max_ctas, (T*)ctx->d_vol,
+                 (const T*)ctx->d_geo};
   ElemArgs<T> la{(const T*)us, (const T*)un, (T*)out, (const T*)ctx->d_flux, ctx->d_eref, (const T*)ctx->d_geo,
-                 (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta};
+                 (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta, ctx->d_err, ctx->E, (const T*)ctx->d_vol};
   const bool prof = ctx->prof && !ctx->capturing;
   cudaStream_t st = ls(ctx);
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -610,15 +622,15 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
     for (auto& e : ev) e = take_event(ctx);
   int rc;
   if (prof) cudaEventRecord(ev[0], st);
-  if constexpr (sizeof(T) == 4) rc = launch_edge32(ctx->N, ea, st);
-  else rc = launch_edge64(ctx->N, ea, st);
+  if constexpr (sizeof(T) == 4) rc = launch_edge_vol32(ctx->N, ea, st);
+  else rc = launch_edge_vol64(ctx->N, ea, st);
   if (prof) {
     cudaEventRecord(ev[1], st);
     cudaEventRecord(ev[2], st);
   }
   if (rc == RDG_OK) {
-    if constexpr (sizeof(T) == 4) rc = launch_elem32(ctx->N, mode, la, st);
-    else rc = launch_elem64(ctx->N, mode, la, st);
+    if constexpr (sizeof(T) == 4) rc = launch_elem_lite32(ctx->N, mode, la, st);
+    else rc = launch_elem_lite64(ctx->N, mode, la, st);
   }
   if (prof) {
     cudaEventRecord(ev[3], st);
@@ -721,6 +733,15 @@ int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps) {
   return RDG_OK;
 }
 
+int rdg_set_launch_limit(rdg_ctx* ctx, int max_ctas) {
+  if (!ctx) return RDG_EINVAL;
+  if (max_ctas < 0) return fail(ctx, RDG_EINVAL, "max_ctas must be >= 0");
+  ctx->max_ctas = max_ctas;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  return RDG_OK;
+}
+
 int rdg_profile(rdg_ctx* ctx, int enable) {
   if (!ctx) return RDG_EINVAL;
   ctx->prof = enable != 0;
@@ -748,6 +769,13 @@ int rdg_synchronize(rdg_ctx* ctx) {
   DeviceGuard g(ctx->device);
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaGetLastError());
+  int h = 0;
+  CK(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    if (h & kErrBadIndex) return fail(ctx, RDG_ECUDA, "a kernel's index self-check failed (corrupt edge tables)");
+    return fail(ctx, RDG_ETIMEOUT, "a bounded device wait gave up (pipeline stalled for more than 2 s)");
+  }
   return RDG_OK;
 }
 

@@ -31,7 +31,7 @@ struct rdg_ctx {
   std::vector<int32_t> eref;     // [3][K]
   // operators
   bool ops_ok = false;
-  int N = 0, prec = RDG_FP32, esz = 4;
+  int N = 0, prec = RDG_FP32, esz = 4, iface = RDG_IFACE_ALG2;
   double vx = 0, vy = 0;
   std::vector<double> Dk;
   // device buffers
@@ -39,7 +39,10 @@ struct rdg_ctx {
   int32_t *d_k1 = nullptr, *d_k2 = nullptr, *d_eref = nullptr;
   void *d_geo = nullptr, *d_flux = nullptr, *d_u = nullptr, *d_u1 = nullptr, *d_u2 = nullptr;
   void *d_S = nullptr, *d_G = nullptr;
+  void* d_vol = nullptr;            // volume terms of the current stage [K][Np]
   TimeState* d_time = nullptr;
+  int* d_err = nullptr;
+  int max_ctas = 0;                // cap on persistent kernel grids (0 = one CTA per SM)            // device error bits (bounded waits that gave up)
   Forcing frc;
   // per-kernel event timing (class 0 edge flux, 1 element update)
   bool prof = false;

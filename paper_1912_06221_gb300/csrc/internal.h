@@ -51,7 +51,16 @@ struct EdgeArgs {
   int64_t E, B;
   Forcing frc;
   TimeArg time;
+  int* err;            // device error word (kErr* bits); may be null
+  int64_t K;           // elements (for the index self-check)
+  int max_ctas;        // cap on the persistent grid (0: one CTA per SM)
+  T* vol;              // fused form: volume term of every element, [K][Np] (else null)
+  const T* geo;        // fused form: element coefficients [6][K]
 };
+
+// Device error bits reported through rdg_synchronize.
+constexpr int kErrWaitTimeout = 1;
+constexpr int kErrBadIndex = 2;
 
 template <typename T>
 struct ElemArgs {
@@ -66,6 +75,9 @@ struct ElemArgs {
   T dt;
   Forcing frc;
   TimeArg time;
+  int* err;            // device error word; may be null
+  int64_t E;           // edges (for the index self-check)
+  const T* vol;        // fused form: precomputed volume term [K][Np] (else null)
 };
 
 // mode: 0 rhs only; 1..3 the three SSP-RK3 stage combinations
@@ -73,6 +85,12 @@ int launch_edge32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 int launch_edge64(int N, const EdgeArgs<double>& a, cudaStream_t s);
 int launch_elem32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s);
 int launch_elem64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s);
+// Fused form: the edge kernel's extra warps also compute the element volume terms (hidden
+// under the operator stream) and the element kernel adds the surface terms and the stage.
+int launch_edge_vol32(int N, const EdgeArgs<float>& a, cudaStream_t s);
+int launch_edge_vol64(int N, const EdgeArgs<double>& a, cudaStream_t s);
+int launch_elem_lite32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s);
+int launch_elem_lite64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s);
 int upload_elem_tables(int device);
 
 // ---- setup (FP64) -------------------------------------------------------------------
@@ -87,6 +105,7 @@ struct EdgeSetupIn {
   const double* refs;      // per-order reference constants (layout in setup.cu)
   int64_t E;
   double vx, vy;
+  int iface;               // RDG_IFACE_*
 };
 
 int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s);

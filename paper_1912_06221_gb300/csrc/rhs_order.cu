@@ -40,4 +40,12 @@ int RDG_CAT(launch_elem_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<
   return launch_elem_t<RDG_REAL, kN>(mode, a, s);
 }
 
+int RDG_CAT(launch_edge_vol_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_REAL>& a, cudaStream_t s) {
+  return launch_edge_t<RDG_REAL, kN, true>(a, s);
+}
+
+int RDG_CAT(launch_elem_lite_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<RDG_REAL>& a, cudaStream_t s) {
+  return launch_elem_t<RDG_REAL, kN, true>(mode, a, s);
+}
+
 }  // namespace rdg

@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(32 * kSetupWarps) edge_setup_kernel(EdgeSetupI
       for (int i = 0; i < NFP; ++i) {
         double c = 0.0;
         for (int j = 0; j < NP; ++j) c += sB[warp][i * NP + j] * Vinv[j * NP + lane];
-        const double Dt = D1v * dvec[i] + D2v * dvec[NFP + i];
+        const double Dt = in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
+                                                         : D1v * dvec[i] + D2v * dvec[NFP + i];
         double w = -Jf * Dt * c;
         if (side == 0 && vn >= 0 && col == (int)fmask[f1 * NFP + i]) w += Jf * vn;
         if (side == 1 && vn < 0 && col == (int)fmask[f2 * NFP + (NFP - 1 - i)]) w += Jf * vn;

@@ -19,6 +19,7 @@ RDG_OK, RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA, RDG_EMESH, RDG_ERANK, RDG_ETIMEOUT, R
 BC_PERIODIC, BC_DIRICHLET = 0, 1
 FP64, FP32 = 0, 1
 TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
+IFACE_ALG2, IFACE_HARMONIC = 0, 1
 ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
 
 # symbol -> (restype, argtypes)
@@ -33,7 +34,7 @@ SIGNATURES = {
     "rdg_create": (_INT, [ctypes.POINTER(_P), _INT, _P]),
     "rdg_destroy": (_INT, [_P]),
     "rdg_mesh_upload": (_INT, [_P, _I64, _P, _I64, _P, _I32, _P]),
-    "rdg_operator_setup": (_INT, [_P, _INT, _P, _D, _D, _INT]),
+    "rdg_operator_setup": (_INT, [_P, _INT, _P, _D, _D, _INT, _INT]),
     "rdg_set_forcing": (_INT, [_P, _INT, _P, _P, _P, _INT, _P, _P, _P]),
     "rdg_mesh_counts": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "rdg_get_node_coords": (_INT, [_P, _P]),
@@ -46,6 +47,7 @@ SIGNATURES = {
     "rdg_solve_to_time": (_INT, [_P, _D, _D, _I64]),
     "rdg_synchronize": (_INT, [_P]),
     "rdg_profile": (_INT, [_P, _INT]),
+    "rdg_set_launch_limit": (_INT, [_P, _INT]),
     "rdg_kernel_stats": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), _INT]),
     "rdg_query_bytes": (_INT, [_INT, _I64, _I64, _I64, _INT, _INT, _INT, ctypes.POINTER(_I64)]),
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
@@ -109,7 +111,7 @@ class Solver:
     """One library context: mesh, operators of order N and the resident state."""
 
     def __init__(self, xy, tri, N: int, D_elem, v=(0.0, 0.0), bc: int = BC_PERIODIC, period=(1.0, 1.0),
-                 precision: int = FP32, device: int = 0, stream=None):
+                 precision: int = FP32, device: int = 0, stream=None, interface: int = IFACE_ALG2):
         import torch
         self.torch = torch
         self.lib = load()
@@ -133,7 +135,7 @@ class Solver:
         self._call("rdg_mesh_upload", xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), bc,
                    _ptr(per) if period is not None else None)
         D = np.ascontiguousarray(np.broadcast_to(np.asarray(D_elem, np.float64), (tri.shape[0],)))
-        self._call("rdg_operator_setup", N, _ptr(D), float(v[0]), float(v[1]), precision)
+        self._call("rdg_operator_setup", N, _ptr(D), float(v[0]), float(v[1]), precision, interface)
         K, E, B = _I64(), _I64(), _I64()
         self._call("rdg_mesh_counts", ctypes.byref(K), ctypes.byref(E), ctypes.byref(B))
         self.K, self.E, self.B = K.value, E.value, B.value
@@ -221,6 +223,10 @@ class Solver:
 
     def synchronize(self):
         self._call("rdg_synchronize")
+
+    def set_launch_limit(self, max_ctas: int):
+        """Cap persistent kernel grids at max_ctas CTAs (0 = one per SM)."""
+        self._call("rdg_set_launch_limit", int(max_ctas))
 
     def profile(self, enable: bool = True):
         self._call("rdg_profile", 1 if enable else 0)

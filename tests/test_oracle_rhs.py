@@ -141,3 +141,33 @@ def test_error_norms_on_exact_interpolant():
     assert l2 < 1e-13 and li < 1e-13
     l2, li = error_norms(m, f(m.x, m.y, 0) + 0.25, f, 0.0)
     assert abs(l2 - 0.25) < 1e-13 and abs(li - 0.25) < 1e-13
+
+
+def _jump_problem(N, interface, m=6):
+    from synth import centroids
+    xy, tri = unit_square_mesh(m, 0.1, 1)
+    me = Mesh(xy, tri, N)
+    cen = centroids(xy, tri)
+    D = np.where(np.hypot(cen[:, 0] - 0.5, cen[:, 1] - 0.5) < 0.25, 1.0, 1e-4)
+    return Problem(me, D, v=(1.0, 0.5), interface=interface)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_high_contrast_jump_stability(N):
+    """Element-wise D with a 1e4 jump across a circle (the circle-pulse recipe on a 6x6x2
+    mesh): with the paper's Algorithm 2 (D~ = mean on the edge) the operator has an
+    eigenvalue with a clearly positive real part; the harmonic interface coefficient gives a
+    stable operator."""
+    lam = np.linalg.eigvals(_jump_problem(N, "alg2").dense_operator())
+    assert lam.real.max() > 1e-2 * np.abs(lam).max()
+    lam = np.linalg.eigvals(_jump_problem(N, "harmonic").dense_operator())
+    assert lam.real.max() < 1e-10 * np.abs(lam).max()
+
+
+def test_interface_rules_agree_for_constant_D():
+    xy, tri = unit_square_mesh(4, 0.1, 2)
+    me = Mesh(xy, tri, 3)
+    u = np.random.default_rng(0).standard_normal((me.K, me.ops.Np))
+    a = Problem(me, np.full(me.K, 0.4), v=(0.3, 0.1), interface="alg2").rhs(u)
+    b = Problem(me, np.full(me.K, 0.4), v=(0.3, 0.1), interface="harmonic").rhs(u)
+    assert np.allclose(a, b, atol=1e-12 * np.abs(a).max())
