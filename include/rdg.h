@@ -154,11 +154,6 @@ int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
  * graph of a fixed chunk of steps (captured on first use for a given dt); enqueued. */
 int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps);
 
-/* Cap the grid of the persistent edge-flux kernel at max_ctas CTAs (0 restores one CTA per
- * SM).  With few CTAs each one streams many operator tiles through its shared-memory ring,
- * which is how the tests exercise the pipeline's wrap-around on small meshes. */
-int rdg_set_launch_limit(rdg_ctx* ctx, int max_ctas);
-
 /* Per-kernel timing.  With enable != 0 every later edge-flux and element-update kernel launch
  * of ctx is bracketed by CUDA events on the context stream (rdg_solve_to_time then steps
  * without its graph).  rdg_kernel_stats waits for the stream and returns, for kernel class

@@ -611,7 +611,7 @@ cudaStream_t ls(const rdg_ctx* ctx) { return ctx->capturing ? ctx->cap_stream : 
 template <typename T>
 int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta) {
   EdgeArgs<T> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const T*)us, (T*)ctx->d_flux, (const T*)ctx->d_G,
-                 ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, ctx->max_ctas, (T*)ctx->d_vol,
+                 ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, (T*)ctx->d_vol,
                  (const T*)ctx->d_geo};
   ElemArgs<T> la{(const T*)us, (const T*)un, (T*)out, (const T*)ctx->d_flux, ctx->d_eref, (const T*)ctx->d_geo,
                  (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta, ctx->d_err, ctx->E, (const T*)ctx->d_vol};
@@ -730,15 +730,6 @@ int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps) {
     int rc = enqueue_rk_step(ctx, ta, dt);
     if (rc != RDG_OK) return fail(ctx, rc, "kernel launch failed");
   }
-  return RDG_OK;
-}
-
-int rdg_set_launch_limit(rdg_ctx* ctx, int max_ctas) {
-  if (!ctx) return RDG_EINVAL;
-  if (max_ctas < 0) return fail(ctx, RDG_EINVAL, "max_ctas must be >= 0");
-  ctx->max_ctas = max_ctas;
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-  ctx->gexec = nullptr;
   return RDG_OK;
 }
 

@@ -41,8 +41,7 @@ struct rdg_ctx {
   void *d_S = nullptr, *d_G = nullptr;
   void* d_vol = nullptr;            // volume terms of the current stage [K][Np]
   TimeState* d_time = nullptr;
-  int* d_err = nullptr;
-  int max_ctas = 0;                // cap on persistent kernel grids (0 = one CTA per SM)            // device error bits (bounded waits that gave up)
+  int* d_err = nullptr;            // device error bits (kernel self-checks)
   Forcing frc;
   // per-kernel event timing (class 0 edge flux, 1 element update)
   bool prof = false;

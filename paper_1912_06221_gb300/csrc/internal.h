@@ -13,7 +13,7 @@ namespace rdg {
 
 constexpr int kTile = 32;            // edges per W tile (one warp, one edge per lane)
 constexpr int kElemBlock = 128;      // elements per element-kernel block
-constexpr int kEdgeBlock = 128;      // edges per edge-kernel block
+constexpr int kStageBlock = 128;     // threads per block of the stage (edge/volume) kernel
 
 // Words (of 16 bytes) per edge row block of the tiled flux operator.
 inline int w_vecs_per_edge(int N, int elem_bytes) {
@@ -53,7 +53,6 @@ struct EdgeArgs {
   TimeArg time;
   int* err;            // device error word (kErr* bits); may be null
   int64_t K;           // elements (for the index self-check)
-  int max_ctas;        // cap on the persistent grid (0: one CTA per SM)
   T* vol;              // fused form: volume term of every element, [K][Np] (else null)
   const T* geo;        // fused form: element coefficients [6][K]
 };

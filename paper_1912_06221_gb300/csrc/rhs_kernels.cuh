@@ -50,87 +50,9 @@ struct Vec16<double> {
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
 
-// ---------------------------------------------------------------------------------------
-// mbarrier / bulk-copy (TMA unit) helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Orders this thread's generic-proxy shared-memory reads before later async-proxy (bulk
-// copy) writes: a slot read with ordinary loads must not be refilled by the copy engine
-// before those loads have read it.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for phase `parity` of an mbarrier, giving up after about two seconds.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-// L2 policy for data streamed once per kernel: evict first, so the operator stream does not
-// push the (L2-resident) state, flux and index arrays out of L2
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-      : "memory");
-}
 __device__ __forceinline__ void report(int* err, int bit) {
   if (err) atomicOr(err, bit);
 }
-
-// Geometry of the streamed operator pipeline for one (T, N); VOL adds the volume warps.
-// Each edge warp owns DEPTH shared-memory slots and keeps DEPTH operator tiles in flight.
-template <typename T, int N, bool VOL = false>
-struct EdgePipe {
-  static constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP;
-  static constexpr int VW = 16 / (int)sizeof(T);
-  static constexpr int QW = (NW + VW - 1) / VW;          // 16-byte words per edge
-  static constexpr int TILE_BYTES = QW * kTile * 16;     // one warp tile of W (contiguous)
-  static constexpr int NV = VOL ? (N <= 4 ? 4 : 2) : 0;  // volume warps
-  static constexpr int VOL_BYTES = NV * kTile * NP * (int)sizeof(T);
-  static constexpr int BAR_BYTES = 1024;
-  static constexpr int BUDGET = 226 * 1024 - BAR_BYTES - VOL_BYTES;
-  static constexpr int SLOTS_RAW = BUDGET / TILE_BYTES;
-  static constexpr int DEPTH = SLOTS_RAW >= 16 ? 3 : 2;  // tiles in flight per edge warp
-  static constexpr int NE_RAW = SLOTS_RAW / DEPTH;
-  static constexpr int NE = NE_RAW > 12 ? 12 : (NE_RAW < 1 ? 1 : NE_RAW);  // edge warps
-  static constexpr int SLOTS = NE * DEPTH;
-  static constexpr int THREADS = 32 * (NE + NV);
-  static constexpr int SMEM = BAR_BYTES + SLOTS * TILE_BYTES + VOL_BYTES;
-  static_assert(SLOTS * 8 + 16 <= BAR_BYTES, "barrier area too small");
-};
 
 // Volume term of one element: M^{-1} S^T . F with F = v u - D grad u, written with the
 // metric-folded coefficients F_r = a_r u - (g_rr u_r + g_rs u_s), F_s = a_s u - (g_rs u_r +
@@ -164,180 +86,6 @@ __device__ __forceinline__ void volume_row(const T (&u)[np_of(N)], T ar, T as, T
   }
 }
 
-// Persistent edge-flux kernel, one CTA per SM (tile = blockIdx.x + m gridDim.x, m taken
-// from a CTA-local counter, so the CTA's warps share its tiles dynamically).  Each edge warp
-// owns DEPTH shared-memory slots: its lane 0 claims a tile, starts a cp.async.bulk of the
-// tile's operator words into a slot (mbarrier completion), and the warp consumes its slots
-// round-robin -- one edge per lane: gather u_k1, u_k2 (L2 resident) while the copy is in
-// flight, wait on the slot's barrier (phase parity = use count, the slot having no other
-// consumer), flux_e = W_e [u1; u2] from shared memory, then fence its shared-memory reads
-// against the async proxy and refill the slot.  Every wait is bounded: on a timeout the
-// kernel sets kErrWaitTimeout, waits (bounded) for the warp's copies in flight and stops.
-//
-// VOL = true (fused form) adds NV volume warps that compute the volume term of element tiles
-// of 32 (tile j = blockIdx.x + m gridDim.x, m = volume warp + NV t) and store it to a.vol;
-// they share the SM with the memory-bound operator stream, so their FMA work is hidden.
-template <typename T, int N, bool VOL>
-__global__ void __launch_bounds__(EdgePipe<T, N, VOL>::THREADS, 1) edge_flux_kernel(EdgeArgs<T> a) {
-  using P = EdgePipe<T, N, VOL>;
-  constexpr int NP = P::NP, NFP = P::NFP, NW = P::NW, QW = P::QW, DEPTH = P::DEPTH, NE = P::NE;
-  using V = Vec16<T>;
-  using VT = typename V::type;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  int* next_tile = reinterpret_cast<int*>(smem + P::SLOTS * 8);
-  unsigned char* ring = smem + P::BAR_BYTES;
-  const int64_t ntiles = (a.E + kTile - 1) / kTile;
-  const int64_t my_n = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < P::SLOTS; ++s) mbar_init(&full[s], 1);
-    *next_tile = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  if constexpr (VOL) {
-    if (warp >= NE) {
-      const int vw = warp - NE;
-      T* sv = reinterpret_cast<T*>(ring + (size_t)P::SLOTS * P::TILE_BYTES) + vw * kTile * NP;
-      const int64_t nvt = (a.K + kTile - 1) / kTile;
-      for (int64_t j = blockIdx.x + (int64_t)vw * gridDim.x; j < nvt; j += (int64_t)P::NV * gridDim.x) {
-        const int64_t k0 = j * kTile;
-        const int nk = (int)min((int64_t)kTile, a.K - k0);
-        const T* src = a.u + k0 * NP;
-        for (int x = lane; x < nk * NP; x += 32) sv[x] = src[x];
-        __syncwarp();
-        T u[NP];
-#pragma unroll
-        for (int jj = 0; jj < NP; ++jj) u[jj] = lane < nk ? sv[lane * NP + jj] : T(0);
-        __syncwarp();
-        if (lane < nk) {
-          const int64_t k = k0 + lane;
-          T vol[NP];
-          volume_row<T, N>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k],
-                           vol);
-#pragma unroll
-          for (int ii = 0; ii < NP; ++ii) sv[lane * NP + ii] = vol[ii];
-        }
-        __syncwarp();
-        T* dst = a.vol + k0 * NP;
-        for (int x = lane; x < nk * NP; x += 32) dst[x] = sv[x];
-        __syncwarp();
-      }
-      return;
-    }
-  }
-
-  const unsigned char* W = static_cast<const unsigned char*>(a.W);
-  const uint64_t pol = l2_evict_first_policy();
-  // claim the CTA's next tile and start its copy into this warp's slot `slot`; returns the
-  // claimed local tile index (warp-uniform) or -1 when the CTA's tiles are exhausted
-  auto issue = [&](int slot) -> long long {
-    long long m = -1;
-    if (lane == 0) {
-      const long long c = atomicAdd(next_tile, 1);
-      if (c < my_n) {
-        m = c;
-        mbar_expect_tx(&full[slot], P::TILE_BYTES);
-        bulk_g2s(ring + (size_t)slot * P::TILE_BYTES, W + (blockIdx.x + c * gridDim.x) * P::TILE_BYTES,
-                 P::TILE_BYTES, &full[slot], pol);
-      }
-    }
-    return __shfl_sync(0xffffffffu, m, 0);
-  };
-  long long ids[DEPTH];
-#pragma unroll
-  for (int d = 0; d < DEPTH; ++d) ids[d] = issue(warp * DEPTH + d);
-
-  // gather u_k1, u_k2 of local tile m into uu (lane = edge); e < 0 when the lane has no edge
-  auto gather = [&](long long m, T (&uu)[2 * NP], int64_t& e) {
-#pragma unroll
-    for (int j = 0; j < 2 * NP; ++j) uu[j] = T(0);
-    e = -1;
-    if (m < 0) return;
-    const int64_t ee = (blockIdx.x + m * gridDim.x) * kTile + lane;
-    if (ee >= a.E) return;
-    e = ee;
-    const int k1 = a.k1[ee], k2 = a.k2[ee];
-    // self-check of the edge table: a bad index is recorded and its access skipped
-    if (k1 < 0 || k1 >= a.K || (k2 >= 0 ? k2 >= a.K : (-1 - (int64_t)k2) >= a.B)) {
-      report(a.err, kErrBadIndex);
-      return;
-    }
-    const T* p1 = a.u + (int64_t)k1 * NP;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) uu[j] = __ldg(p1 + j);
-    if (k2 >= 0) {
-      const T* p2 = a.u + (int64_t)k2 * NP;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) uu[NP + j] = __ldg(p2 + j);
-    } else {
-      // ghost side of a boundary edge: g = sum_m G_m tau_m(t)
-      const int64_t b = -1 - (int64_t)k2;
-      const double t = stage_time(a.time);
-      for (int mm = 0; mm < a.frc.nghost; ++mm) {
-        const T tm = (T)tau_of(a.frc.gkind[mm], a.frc.gomega[mm], t);
-        const T* g = a.G + ((int64_t)mm * a.B + b) * NP;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) uu[NP + j] += tm * g[j];
-      }
-    }
-  };
-
-  // one tile: prefetch the next tile's gathers into nxt, wait for this tile's operator words,
-  // flux = W [u1; u2] with cur, refill the slot; false when the warp has no tile left
-  auto step = [&](int k, T (&cur)[2 * NP], int64_t ecur, T (&nxt)[2 * NP], int64_t& enxt) -> bool {
-    const int d = k % DEPTH;
-    const int slot = warp * DEPTH + d;
-    if (ids[d] < 0) return false;
-    gather(ids[(k + 1) % DEPTH], nxt, enxt);
-    const bool landed = __all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (uint32_t)(k / DEPTH) & 1u));
-    if (!landed) {
-      if (lane == 0) {
-        report(a.err, kErrWaitTimeout);
-        // let this warp's other copies in flight land before it leaves
-        for (int dd = 1; dd < DEPTH; ++dd) {
-          const int kk = k + dd;
-          if (ids[kk % DEPTH] >= 0) mbar_wait_bounded(&full[warp * DEPTH + kk % DEPTH], (uint32_t)(kk / DEPTH) & 1u);
-        }
-      }
-      return false;
-    }
-    const VT* w = reinterpret_cast<const VT*>(ring + (size_t)slot * P::TILE_BYTES) + lane;
-    T acc[NFP];
-#pragma unroll
-    for (int i2 = 0; i2 < NFP; ++i2) acc[i2] = T(0);
-#pragma unroll
-    for (int q = 0; q < QW; ++q) {
-      const VT v = w[q * kTile];
-#pragma unroll
-      for (int cc = 0; cc < V::n; ++cc) {
-        const int idx = q * V::n + cc;
-        if (idx < NW) acc[idx / (2 * NP)] = fma(V::get(v, cc), cur[idx % (2 * NP)], acc[idx / (2 * NP)]);
-      }
-    }
-    // the slot's reads (generic proxy) must be ordered before the copy engine refills it
-    fence_proxy_async_smem();
-    __syncwarp();
-    ids[d] = issue(slot);
-    if (ecur >= 0) {
-      T* o = a.flux + ecur * NFP;
-#pragma unroll
-      for (int r = 0; r < NFP; ++r) o[r] = acc[r];
-    }
-    return true;
-  };
-
-  T ua[2 * NP], ub[2 * NP];
-  int64_t ea, eb;
-  gather(ids[0], ua, ea);
-  for (int k = 0;; k += 2) {
-    if (!step(k, ua, ea, ub, eb)) break;
-    if (!step(k + 1, ub, eb, ua, ea)) break;
-  }
-}
-
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void stage_in(T* sh, const T* g, int n) {
@@ -357,6 +105,119 @@ __device__ __forceinline__ void stage_out(T* g, const T* sh, int n) {
   const float4* s4 = reinterpret_cast<const float4*>(sh);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) __stcs(g4 + i, s4[i]);
   for (int i = nv * V + threadIdx.x; i < n; i += blockDim.x) g[i] = sh[i];
+}
+
+// Volume role of the stage kernel: element tile v (one thread per element, rows staged
+// through shared memory), vol = M^{-1} S^T . F written to a.vol.  Kept out of line so its
+// register demand does not set the edge role's.
+template <typename T, int N>
+__device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, T* sh) {
+  constexpr int NP = np_of(N);
+  const int tid = threadIdx.x;
+  const int64_t k0 = v * kStageBlock;
+  const int nk = (int)min((int64_t)kStageBlock, a.K - k0);
+  stage_in(sh, a.u + k0 * NP, nk * NP);
+  __syncthreads();
+  if (tid < nk) {
+    const int64_t k = k0 + tid;
+    T u[NP], vol[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) u[j] = sh[tid * NP + j];
+    volume_row<T, N>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k], vol);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) sh[tid * NP + j] = vol[j];   // a thread rewrites only its own row
+  }
+  __syncthreads();
+  stage_out(a.vol + k0 * NP, sh, nk * NP);
+}
+
+// Edge role of the stage kernel: edge e (one thread per edge), flux_e = W_e [u_k1; u_k2].
+// The gathers hit L2; the operator words are streamed with evict-first 16-byte loads (a warp
+// reads 512 contiguous bytes per load of its tile).
+template <typename T, int N>
+__device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
+  constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP;
+  using V = Vec16<T>;
+  using VT = typename V::type;
+  constexpr int QW = (NW + V::n - 1) / V::n;
+  const int k1 = a.k1[e], k2 = a.k2[e];
+  T u1[NP], u2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) u1[j] = u2[j] = T(0);
+  // self-check of the edge table: a bad index is recorded and its access skipped
+  if (k1 < 0 || k1 >= a.K || (k2 >= 0 ? k2 >= a.K : (-1 - (int64_t)k2) >= a.B)) {
+    report(a.err, kErrBadIndex);
+  } else {
+    const T* p1 = a.u + (int64_t)k1 * NP;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) u1[j] = __ldg(p1 + j);
+    if (k2 >= 0) {
+      const T* p2 = a.u + (int64_t)k2 * NP;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) u2[j] = __ldg(p2 + j);
+    } else {
+      // ghost side of a boundary edge: g = sum_m G_m tau_m(t)
+      const int64_t bb = -1 - (int64_t)k2;
+      const double t = stage_time(a.time);
+      for (int mm = 0; mm < a.frc.nghost; ++mm) {
+        const T tm = (T)tau_of(a.frc.gkind[mm], a.frc.gomega[mm], t);
+        const T* g = a.G + ((int64_t)mm * a.B + bb) * NP;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) u2[j] += tm * g[j];
+      }
+    }
+  }
+  const VT* w = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
+  T acc[NFP];
+#pragma unroll
+  for (int r = 0; r < NFP; ++r) acc[r] = T(0);
+#pragma unroll
+  for (int q = 0; q < QW; ++q) {
+    const VT v = ld_stream(w + q * kTile);
+#pragma unroll
+    for (int cc = 0; cc < V::n; ++cc) {
+      const int idx = q * V::n + cc;
+      if (idx < NW) {
+        const int r = idx / (2 * NP), j = idx % (2 * NP);
+        acc[r] = fma(V::get(v, cc), j < NP ? u1[j] : u2[j - NP], acc[r]);
+      }
+    }
+  }
+  T* o = a.flux + e * NFP;
+#pragma unroll
+  for (int r = 0; r < NFP; ++r) o[r] = acc[r];
+}
+
+// Stage kernel: one block per tile.  Without VOL every block is an edge block; with VOL (the
+// fused form) the ceil(E/128) edge blocks and ceil(K/128) volume blocks are interleaved
+// evenly over the grid (block b is a volume block when floor((b+1) nv / nb) steps up), so
+// the volume FMAs run on the same SMs while the operator stream keeps HBM busy.
+// Resident stage blocks per SM asked of the compiler (FP32: 5 blocks up to N = 4, <= 102
+// registers; 4 above; FP64: 4 up to N = 3, 3 above), so the operator stream keeps enough
+// loads in flight.
+template <typename T, int N>
+constexpr int stage_min_blocks() {
+  return sizeof(T) == 4 ? (N <= 4 ? 5 : 4) : (N <= 3 ? 4 : 3);
+}
+
+template <typename T, int N, bool VOL>
+__global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_flux_kernel(EdgeArgs<T> a) {
+  constexpr int NP = np_of(N);
+  int64_t eblk = blockIdx.x;
+  if constexpr (VOL) {
+    __shared__ __align__(16) T sh[kStageBlock * NP];
+    const int64_t nb = gridDim.x;
+    const int64_t nv = (a.K + kStageBlock - 1) / kStageBlock;
+    const int64_t b = blockIdx.x;
+    const int64_t v0 = (b * nv) / nb, v1 = ((b + 1) * nv) / nb;
+    if (v1 > v0) {
+      stage_volume_tile<T, N>(a, v0, sh);
+      return;
+    }
+    eblk = b - v1;    // edge blocks so far = blocks so far minus volume blocks so far
+  }
+  const int64_t e = eblk * kStageBlock + threadIdx.x;
+  if (e < a.E) stage_edge<T, N>(a, e);
 }
 
 // Resident blocks per SM asked of the compiler for the surface-only form (VOLIN): FP32 orders
@@ -566,23 +427,10 @@ inline int sm_count() {
 
 template <typename T, int N, bool VOL = false>
 inline int launch_edge_t(const EdgeArgs<T>& a, cudaStream_t s) {
-  using P = dev::EdgePipe<T, N, VOL>;
-  if (a.E == 0) return RDG_OK;
-  static bool attr_set[64] = {false};   // per instantiation and device
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return RDG_EINVAL;
-  if (!attr_set[dev]) {
-    if (cudaFuncSetAttribute(dev::edge_flux_kernel<T, N, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             P::SMEM) != cudaSuccess)
-      return RDG_ECUDA;
-    attr_set[dev] = true;
-  }
-  const int64_t ntiles = (a.E + kTile - 1) / kTile;
-  int64_t cap = sm_count();
-  if (a.max_ctas > 0 && a.max_ctas < cap) cap = a.max_ctas;
-  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, cap);
-  dev::edge_flux_kernel<T, N, VOL><<<grid, P::THREADS, P::SMEM, s>>>(a);
+  if (a.E == 0 && (!VOL || a.K == 0)) return RDG_OK;
+  int64_t grid = (a.E + kStageBlock - 1) / kStageBlock;
+  if (VOL) grid += (a.K + kStageBlock - 1) / kStageBlock;
+  dev::edge_flux_kernel<T, N, VOL><<<(unsigned)grid, kStageBlock, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
 

@@ -67,14 +67,14 @@ extern "C" int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_de
     TimeArg ta{nullptr, t, 1.0, 0.0};
     if (ctx->esz == 4) {
       EdgeArgs<float> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const float*)u_dev, (float*)flux, (const float*)ctx->d_G,
-                         ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, ctx->max_ctas};
+                         ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K};
       ElemArgs<float> la{(const float*)u_dev, nullptr, (float*)rhs_dev, (const float*)flux, ctx->d_eref,
                          (const float*)ctx->d_geo, (const float*)ctx->d_S, ctx->K, 0.0f, ctx->frc, ta, ctx->d_err, ctx->E};
       rc = launch_edge32(ctx->N, ea, ctx->stream);
       if (rc == RDG_OK) rc = launch_elem32(ctx->N, 0, la, ctx->stream);
     } else {
       EdgeArgs<double> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const double*)u_dev, (double*)flux, (const double*)ctx->d_G,
-                          ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, ctx->max_ctas};
+                          ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K};
       ElemArgs<double> la{(const double*)u_dev, nullptr, (double*)rhs_dev, (const double*)flux, ctx->d_eref,
                           (const double*)ctx->d_geo, (const double*)ctx->d_S, ctx->K, 0.0, ctx->frc, ta, ctx->d_err, ctx->E};
       rc = launch_edge64(ctx->N, ea, ctx->stream);

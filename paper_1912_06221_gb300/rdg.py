@@ -47,7 +47,6 @@ SIGNATURES = {
     "rdg_solve_to_time": (_INT, [_P, _D, _D, _I64]),
     "rdg_synchronize": (_INT, [_P]),
     "rdg_profile": (_INT, [_P, _INT]),
-    "rdg_set_launch_limit": (_INT, [_P, _INT]),
     "rdg_kernel_stats": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), _INT]),
     "rdg_query_bytes": (_INT, [_INT, _I64, _I64, _I64, _INT, _INT, _INT, ctypes.POINTER(_I64)]),
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
@@ -223,10 +222,6 @@ class Solver:
 
     def synchronize(self):
         self._call("rdg_synchronize")
-
-    def set_launch_limit(self, max_ctas: int):
-        """Cap persistent kernel grids at max_ctas CTAs (0 = one per SM)."""
-        self._call("rdg_set_launch_limit", int(max_ctas))
 
     def profile(self, enable: bool = True):
         self._call("rdg_profile", 1 if enable else 0)

@@ -234,12 +234,10 @@ def test_error_paths():
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
-@pytest.mark.parametrize("max_ctas", [1, 3])
-def test_rhs_parity_deep_pipeline(N, prec, max_ctas):
-    """With the persistent edge kernel capped at 1 or 3 CTAs, each CTA streams tens of
-    operator tiles through its shared-memory ring (many wrap-arounds of every slot)."""
+def test_rhs_parity_larger_mesh(N, prec):
+    """20x20x2 Dirichlet mesh: 1200 edges (38 edge tiles) and 800 elements (7 element tiles,
+    interleaved with the edge tiles in the stage kernel's grid)."""
     s, me, D = _setup(N, m=20, prec=prec, bc=DIRICHLET)
-    s.set_launch_limit(max_ctas)
     osrc, gfn = _forcing(s, me)
     pr = Problem(me, D, v=(0.7, -0.4), source=osrc, ghost_fn=gfn)
     u = random_nodal(s.K, s.Np, 21)
@@ -253,9 +251,8 @@ def test_rhs_parity_deep_pipeline(N, prec, max_ctas):
 
 @pytest.mark.parametrize("prec", [rdg.FP32, rdg.FP64])
 def test_repeatable_at_scale(prec):
-    """A 160x160x2 mesh (76800 edges, several pipeline wraps per CTA at one CTA per SM):
-    repeated right-hand sides and a graph-replayed solve are bitwise repeatable and every
-    bounded wait completes."""
+    """A 160x160x2 mesh (76800 edges): repeated right-hand sides and a graph-replayed solve are
+    bitwise repeatable and no kernel self-check fires."""
     xy, tri = unit_square_mesh(160, 0.1, 5)
     s = rdg.Solver(xy, tri, 4, 0.3, v=(0.2, 0.1), precision=prec)
     u = torch.tensor(random_nodal(s.K, s.Np, 3), dtype=s.dtype, device="cuda")
