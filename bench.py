@@ -50,11 +50,27 @@ def parse():
     p.add_argument("--rk-steps", type=int, default=RK_STEPS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--serve", action="store_true", help="run the request-stream server instead")
+    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--serve-slots", type=int, default=32)
     return p.parse_args()
 
 
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def aggregate(t_ms_local, units_local, dist=None, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time (max over ranks)
+    and the units of all ranks.  Returns (t_ms_max, units_total, units_total / t_max)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t_ms_local, units_local, units_local / (t_ms_local / 1e3)
+    t = torch.tensor([float(t_ms_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t), float(n), float(n) / (float(t) / 1e3)
 
 
 # ---------------------------------------------------------------------------------------
@@ -252,13 +268,9 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt)
-    dofs = s.K * s.Np * 3 * nrk * args.steps * world
-    value = dofs / (t_ms / 1e3) / 1e9
+    t_local = sum(a.elapsed_time(b) for a, b in evs)
+    t_ms, dofs, rate = aggregate(t_local, s.K * s.Np * 3 * nrk * args.steps, dist, device="cuda")
+    value = rate / 1e9
     u_fp32 = s.get_state_host().astype(np.float64)
 
     # per-kernel times (event-bracketed launches of one more solve)
@@ -357,9 +369,53 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Poisson stream of solve requests (rate 200/s, seed 3): jittered periodic meshes of
+    log-uniform size 1e3..1e6 triangles, N in 2..6, element-wise D with a log-uniform contrast
+    in [1, 1e4] across a random circle, v in [-1,1]^2, 50..500 SSP-RK3 steps, FP32, 120 GB
+    admission budget; FP64 spot check of the requests the stream marks (1%).  Prints one
+    JSON line with p50/p99 latency and the aggregate GDOF/s."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06221_gb300 as rdg
+    from paper_1912_06221_gb300.serve import Server, SolveRequest, latency_stats, solve_alone
+    from synth import serve_stream
+    stream = serve_stream(seed=3, nreq=args.serve_requests, rate=200.0, build_mesh=False)
+    reqs = []
+    for r in stream:
+        w = r.workload
+        reqs.append(SolveRequest(r.rid, r.arrival, None, None, w.N, None, w.v, w.u0, w.steps,
+                                 build=w.meta["build"], n_triangles=w.meta["triangles"]))
+    srv = Server(budget_bytes=120 * 10 ** 9, max_slots=args.serve_slots, chunk=16)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    st = latency_stats(res)
+    by_id = {r.rid: r for r in res}
+    checks = []
+    for r in stream:
+        if r.fp64_check:
+            got = by_id[r.rid]
+            ref = solve_alone(reqs[r.rid], got.dt, precision=rdg.FP64)
+            checks.append({"rid": r.rid, "triangles": got.K, "N": reqs[r.rid].N,
+                           "fp32_rel_l2_vs_fp64": float(np.linalg.norm(got.state - ref) / np.linalg.norm(ref))})
+    line = {"metric": "serve p50/p99 latency and aggregate GDOF/s", "value": st["gdof_per_s"], "unit": "GDOF/s",
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"], "n_requests": st["n"],
+            "makespan_s": st["makespan_s"], "wall_s": wall, "peak_admitted_bytes": srv.peak_in_use,
+            "max_resident": srv.max_concurrent, "budget_bytes": srv.budget, "fp64_spot_checks": checks,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Poisson stream, rate 200/s, seed 3, %d requests, K log-uniform 1e3..1e6, "
+                                   "N 2..6, D contrast log-uniform 1..1e4 across a random circle, 50..500 steps"
+                                   % args.serve_requests}}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serve:
+        run_serve(a)
     else:
         run_ours(a)

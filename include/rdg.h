@@ -154,6 +154,12 @@ int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
  * graph of a fixed chunk of steps (captured on first use for a given dt); enqueued. */
 int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps);
 
+/* Bytes of the per-edge flux operators that every stage loads with an evict-last L2 policy,
+ * so they stay L2-resident from one stage to the next instead of streaming from HBM again
+ * (the rest is streamed evict-first).  -1 (the default) and 0 stream everything.  Affects
+ * speed only, never results. */
+int rdg_set_l2_resident_bytes(rdg_ctx* ctx, int64_t bytes);
+
 /* Per-kernel timing.  With enable != 0 every later edge-flux and element-update kernel launch
  * of ctx is bracketed by CUDA events on the context stream (rdg_solve_to_time then steps
  * without its graph).  rdg_kernel_stats waits for the stream and returns, for kernel class

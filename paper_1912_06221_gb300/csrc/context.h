@@ -40,8 +40,11 @@ struct rdg_ctx {
   void *d_geo = nullptr, *d_flux = nullptr, *d_u = nullptr, *d_u1 = nullptr, *d_u2 = nullptr;
   void *d_S = nullptr, *d_G = nullptr;
   void* d_vol = nullptr;            // volume terms of the current stage [K][Np]
+  void* d_fb = nullptr;             // face fluxes of the current stage [K][3][Nfp]
+  int32_t* d_f12 = nullptr;         // per edge f1 | f2 << 2
   TimeState* d_time = nullptr;
   int* d_err = nullptr;            // device error bits (kernel self-checks)
+  int64_t l2_keep_bytes = -1;       // operator bytes kept L2-resident (-1: default)
   Forcing frc;
   // per-kernel event timing (class 0 edge flux, 1 element update)
   bool prof = false;

@@ -55,6 +55,9 @@ struct EdgeArgs {
   int64_t K;           // elements (for the index self-check)
   T* vol;              // fused form: volume term of every element, [K][Np] (else null)
   const T* geo;        // fused form: element coefficients [6][K]
+  const int32_t* f12;  // fused form: per edge f1 | f2 << 2 (local faces of the two sides)
+  T* fb;               // fused form: face fluxes [K][3][Nfp] in each element's own face order
+  int64_t keep_tiles;  // operator tiles [0, keep_tiles) are loaded evict-last (kept in L2)
 };
 
 // Device error bits reported through rdg_synchronize.
@@ -77,6 +80,7 @@ struct ElemArgs {
   int* err;            // device error word; may be null
   int64_t E;           // edges (for the index self-check)
   const T* vol;        // fused form: precomputed volume term [K][Np] (else null)
+  const T* fb;         // fused form: face fluxes [K][3][Nfp]
 };
 
 // mode: 0 rhs only; 1..3 the three SSP-RK3 stage combinations

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "internal.h"
 
@@ -49,6 +50,31 @@ struct Vec16<double> {
 // streaming (evict-first) 16-byte load for data read once per kernel
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
+
+// 16-byte load that asks L2 to keep the line (evict-last policy): operator words reread by
+// every stage stay L2-resident up to the keep budget instead of streaming from HBM again
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ld_keep(const float4* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_keep(const double2* p, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream finishes; it must wait here before touching any
+// data the predecessor reads or writes (a no-op for an ordinary launch).
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void report(int* err, int bit) {
   if (err) atomicOr(err, bit);
@@ -97,6 +123,39 @@ __device__ __forceinline__ void stage_in(T* sh, const T* g, int n) {
   for (int i = nv * V + threadIdx.x; i < n; i += blockDim.x) sh[i] = g[i];
 }
 
+// Batched staging: every thread first issues all of its 16-byte loads of a block's rows
+// (n values, n <= BLK * NP, 16-byte aligned start) into registers, and only then stores them
+// to shared memory, so a tile costs one memory round trip instead of one per loop trip.
+template <typename T, int BLK, int NP>
+struct Staged {
+  static constexpr int V = 16 / (int)sizeof(T);
+  static constexpr int IT = ((BLK * NP + V - 1) / V + BLK - 1) / BLK;
+  float4 r[IT];
+  T tail0;
+  __device__ __forceinline__ void load(const T* g, int n) {
+    const int nv = n / V;
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int i = threadIdx.x + it * BLK;
+      if (i < nv) r[it] = __ldcs(g4 + i);
+    }
+    const int i = nv * V + threadIdx.x;
+    if (threadIdx.x < V && i < n) tail0 = g[i];
+  }
+  __device__ __forceinline__ void store(T* sh, int n) const {
+    const int nv = n / V;
+    float4* s4 = reinterpret_cast<float4*>(sh);
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int i = threadIdx.x + it * BLK;
+      if (i < nv) s4[i] = r[it];
+    }
+    const int i = nv * V + threadIdx.x;
+    if (threadIdx.x < V && i < n) sh[i] = tail0;
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ void stage_out(T* g, const T* sh, int n) {
   constexpr int V = 16 / sizeof(T);
@@ -116,7 +175,11 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
   const int tid = threadIdx.x;
   const int64_t k0 = v * kStageBlock;
   const int nk = (int)min((int64_t)kStageBlock, a.K - k0);
-  stage_in(sh, a.u + k0 * NP, nk * NP);
+  {
+    Staged<T, kStageBlock, NP> g;
+    g.load(a.u + k0 * NP, nk * NP);
+    g.store(sh, nk * NP);
+  }
   __syncthreads();
   if (tid < nk) {
     const int64_t k = k0 + tid;
@@ -134,7 +197,7 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
 // Edge role of the stage kernel: edge e (one thread per edge), flux_e = W_e [u_k1; u_k2].
 // The gathers hit L2; the operator words are streamed with evict-first 16-byte loads (a warp
 // reads 512 contiguous bytes per load of its tile).
-template <typename T, int N>
+template <typename T, int N, bool FB>
 __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
   constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP;
   using V = Vec16<T>;
@@ -168,12 +231,14 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
     }
   }
   const VT* w = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
+  const bool keep = (e >> 5) < a.keep_tiles;
+  const uint64_t pol = keep ? l2_keep_policy() : 0;
   T acc[NFP];
 #pragma unroll
   for (int r = 0; r < NFP; ++r) acc[r] = T(0);
 #pragma unroll
   for (int q = 0; q < QW; ++q) {
-    const VT v = ld_stream(w + q * kTile);
+    const VT v = keep ? ld_keep(w + q * kTile, pol) : ld_stream(w + q * kTile);
 #pragma unroll
     for (int cc = 0; cc < V::n; ++cc) {
       const int idx = q * V::n + cc;
@@ -183,9 +248,25 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
       }
     }
   }
-  T* o = a.flux + e * NFP;
+  if constexpr (FB) {
+    // scatter to the two elements' face slots: side 1 in its face order, side 2 (outward
+    // normal -n1, face traversed the other way) negated and reversed
+    const int f12 = a.f12[e];
+    if (k1 >= 0 && k1 < a.K) {
+      T* o1 = a.fb + ((int64_t)k1 * 3 + (f12 & 3)) * NFP;
 #pragma unroll
-  for (int r = 0; r < NFP; ++r) o[r] = acc[r];
+      for (int r = 0; r < NFP; ++r) o1[r] = acc[r];
+    }
+    if (k2 >= 0 && k2 < a.K) {
+      T* o2 = a.fb + ((int64_t)k2 * 3 + ((f12 >> 2) & 3)) * NFP;
+#pragma unroll
+      for (int r = 0; r < NFP; ++r) o2[r] = -acc[NFP - 1 - r];
+    }
+  } else {
+    T* o = a.flux + e * NFP;
+#pragma unroll
+    for (int r = 0; r < NFP; ++r) o[r] = acc[r];
+  }
 }
 
 // Stage kernel: one block per tile.  Without VOL every block is an edge block; with VOL (the
@@ -203,6 +284,7 @@ constexpr int stage_min_blocks() {
 template <typename T, int N, bool VOL>
 __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_flux_kernel(EdgeArgs<T> a) {
   constexpr int NP = np_of(N);
+  wait_for_predecessor();
   int64_t eblk = blockIdx.x;
   if constexpr (VOL) {
     __shared__ __align__(16) T sh[kStageBlock * NP];
@@ -217,15 +299,15 @@ __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_fl
     eblk = b - v1;    // edge blocks so far = blocks so far minus volume blocks so far
   }
   const int64_t e = eblk * kStageBlock + threadIdx.x;
-  if (e < a.E) stage_edge<T, N>(a, e);
+  if (e < a.E) stage_edge<T, N, VOL>(a, e);
 }
 
 // Resident blocks per SM asked of the compiler for the surface-only form (VOLIN): FP32 orders
-// up to 4 fit 8 blocks of 128 threads (<= 64 registers), so a 131072-element stage runs in
-// one wave.
+// up to 4 fit 7 blocks of 128 threads (<= 73 registers), so a 131072-element stage (1024
+// blocks) runs in one wave on 152 SMs.
 template <typename T, int N, bool VOLIN>
 constexpr int elem_min_blocks() {
-  return (VOLIN && sizeof(T) == 4 && N <= 4) ? 8 : 1;
+  return (VOLIN && sizeof(T) == 4 && N <= 4) ? 7 : 1;
 }
 
 // Element update.  VOLIN = false: volume term computed here; VOLIN = true: read from a.vol
@@ -318,22 +400,23 @@ __global__ void __launch_bounds__(kElemBlock, elem_min_blocks<T, N, VOLIN>()) el
 }
 
 // Surface-only element update of the fused form: rhs = vol - (1/J) sum_f LIFT_f q_f + s,
-// then the stage.  All of the block's inputs are requested up front (edge ids and face
-// fluxes into registers, volume term / stage input / step start through shared memory), so
-// one memory round trip covers the kernel.
-// Elements per block of the surface-only kernel: 128, or 64 where three staged arrays of
-// 128 rows would pass the 48 KB static shared-memory limit (FP64, N >= 5).
+// then the stage.  The edge kernel has already scattered each edge's flux into both
+// elements' face slots (q), so every input is a contiguous [K][.] row: the block stages its
+// rows of the volume term, face fluxes, stage input and step start in one round trip.
 template <typename T, int N>
 __host__ __device__ constexpr int lite_block() {
-  return 3 * 128 * np_of(N) * (int)sizeof(T) > 46 * 1024 ? 64 : 128;
+  return 128 * (3 * np_of(N) + 3 * nfp_of(N)) * (int)sizeof(T) <= 46 * 1024
+             ? 128
+             : (64 * (3 * np_of(N) + 3 * nfp_of(N)) * (int)sizeof(T) <= 46 * 1024 ? 64 : 32);
 }
 
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true>()) elem_lite_kernel(ElemArgs<T> a) {
-  constexpr int NP = np_of(N), NFP = nfp_of(N);
+  constexpr int NP = np_of(N), NFP = nfp_of(N), NQ = 3 * NFP;
   constexpr int OLIFT = 4 * NP * NP;
   constexpr int BLK = lite_block<T, N>();
   __shared__ __align__(16) T shv[BLK * NP];
+  __shared__ __align__(16) T shq[BLK * NQ];
   __shared__ __align__(16) T shs[MODE >= 1 ? BLK * NP : 4];
   __shared__ __align__(16) T shn[MODE >= 2 ? BLK * NP : 4];
   __shared__ T tau_s[RDG_MAX_FORCING_TERMS];
@@ -342,48 +425,37 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
   const int tid = threadIdx.x;
   const bool active = tid < nk;
   const int64_t k = k0 + tid;
+  wait_for_predecessor();
 
-  int er[3] = {0, 0, 0};
-  T ij = T(0);
-  if (active) {
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      er[f] = a.eref[(int64_t)f * a.K + k];
-      if (er[f] < 0 || (er[f] >> 1) >= a.E) {     // self-check: record and read edge 0 instead
-        report(a.err, kErrBadIndex);
-        er[f] = 0;
-      }
-    }
-    ij = a.geo[5 * a.K + k];
+  {
+    Staged<T, BLK, NP> gv, gs, gn;
+    Staged<T, BLK, NQ> gq;
+    gv.load(a.vol + k0 * NP, nk * NP);
+    gq.load(a.fb + k0 * NQ, nk * NQ);
+    if (MODE >= 1) gs.load(a.us + k0 * NP, nk * NP);
+    if (MODE >= 2) gn.load(a.un + k0 * NP, nk * NP);
+    gv.store(shv, nk * NP);
+    gq.store(shq, nk * NQ);
+    if (MODE >= 1) gs.store(shs, nk * NP);
+    if (MODE >= 2) gn.store(shn, nk * NP);
   }
-  stage_in(shv, a.vol + k0 * NP, nk * NP);
-  if (MODE >= 1) stage_in(shs, a.us + k0 * NP, nk * NP);
-  if (MODE >= 2) stage_in(shn, a.un + k0 * NP, nk * NP);
-  T q[3][NFP];
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    const T* fl = a.flux + (int64_t)(er[f] >> 1) * NFP;
-#pragma unroll
-    for (int c = 0; c < NFP; ++c) q[f][c] = active ? fl[c] : T(0);
-  }
+  const T ij = active ? a.geo[5 * a.K + k] : T(0);
   if (tid < a.frc.nsrc) tau_s[tid] = (T)tau_of(a.frc.kind[tid], a.frc.omega[tid], stage_time(a.time));
   __syncthreads();
 
   T rhs[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) rhs[i] = shv[tid * NP + i];
-  // surface terms: side 1 takes J_f F*.n1 in its face order, side 2 the negated reverse
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
-    const bool side2 = er[f] & 1;
-    T qv[NFP];
+    T q[NFP];
 #pragma unroll
-    for (int c = 0; c < NFP; ++c) qv[c] = side2 ? -q[f][NFP - 1 - c] : q[f][c];
+    for (int c = 0; c < NFP; ++c) q[c] = shq[tid * NQ + f * NFP + c];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < NFP; ++c) acc = fma((T)RDG_TAB[OLIFT + i * 3 * NFP + f * NFP + c], qv[c], acc);
+      for (int c = 0; c < NFP; ++c) acc = fma((T)RDG_TAB[OLIFT + i * 3 * NFP + f * NFP + c], q[c], acc);
       rhs[i] -= ij * acc;
     }
   }
@@ -412,6 +484,23 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
 }  // namespace dev
 
 // Host-side launch helpers instantiated by the including translation unit.
+// Launch with programmatic stream serialization (the kernel waits for its predecessor with
+// griddepcontrol.wait), so its launch and block scheduling overlap the predecessor's tail.
+template <typename... KArgs, typename... Args>
+inline int launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...) == cudaSuccess ? RDG_OK : RDG_ECUDA;
+}
+
 inline int sm_count() {
   static int cached[64] = {0};
   int dev = 0;
@@ -430,6 +519,7 @@ inline int launch_edge_t(const EdgeArgs<T>& a, cudaStream_t s) {
   if (a.E == 0 && (!VOL || a.K == 0)) return RDG_OK;
   int64_t grid = (a.E + kStageBlock - 1) / kStageBlock;
   if (VOL) grid += (a.K + kStageBlock - 1) / kStageBlock;
+  if constexpr (VOL) return launch_pdl(dev::edge_flux_kernel<T, N, VOL>, (unsigned)grid, kStageBlock, s, a);
   dev::edge_flux_kernel<T, N, VOL><<<(unsigned)grid, kStageBlock, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
@@ -442,10 +532,10 @@ inline int launch_elem_t(int mode, const ElemArgs<T>& a, cudaStream_t s) {
     constexpr int BLK = dev::lite_block<T, N>();
     const unsigned g2 = (unsigned)((a.K + BLK - 1) / BLK);
     switch (mode) {
-      case 0: dev::elem_lite_kernel<T, N, 0><<<g2, BLK, 0, s>>>(a); break;
-      case 1: dev::elem_lite_kernel<T, N, 1><<<g2, BLK, 0, s>>>(a); break;
-      case 2: dev::elem_lite_kernel<T, N, 2><<<g2, BLK, 0, s>>>(a); break;
-      case 3: dev::elem_lite_kernel<T, N, 3><<<g2, BLK, 0, s>>>(a); break;
+      case 0: return launch_pdl(dev::elem_lite_kernel<T, N, 0>, g2, BLK, s, a);
+      case 1: return launch_pdl(dev::elem_lite_kernel<T, N, 1>, g2, BLK, s, a);
+      case 2: return launch_pdl(dev::elem_lite_kernel<T, N, 2>, g2, BLK, s, a);
+      case 3: return launch_pdl(dev::elem_lite_kernel<T, N, 3>, g2, BLK, s, a);
       default: return RDG_EINVAL;
     }
   } else {

@@ -47,6 +47,7 @@ SIGNATURES = {
     "rdg_solve_to_time": (_INT, [_P, _D, _D, _I64]),
     "rdg_synchronize": (_INT, [_P]),
     "rdg_profile": (_INT, [_P, _INT]),
+    "rdg_set_l2_resident_bytes": (_INT, [_P, _I64]),
     "rdg_kernel_stats": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), _INT]),
     "rdg_query_bytes": (_INT, [_INT, _I64, _I64, _I64, _INT, _INT, _INT, ctypes.POINTER(_I64)]),
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
@@ -222,6 +223,10 @@ class Solver:
 
     def synchronize(self):
         self._call("rdg_synchronize")
+
+    def set_l2_resident_bytes(self, nbytes: int):
+        """Operator bytes kept L2-resident across stages (-1 default = 0 = none); speed only."""
+        self._call("rdg_set_l2_resident_bytes", int(nbytes))
 
     def profile(self, enable: bool = True):
         self._call("rdg_profile", 1 if enable else 0)

@@ -188,6 +188,14 @@ def batched_heat(seed: int = 2, nprob: int = 64, side_lo: int = 8, side_hi: int 
     return out
 
 
+def _circle_mesh(m, mesh_seed, cx, cy, rad, inside_high, contrast):
+    xy, tri = unit_square_mesh(m, 0.1, mesh_seed)
+    cen = centroids(xy, tri)
+    ins = np.hypot(cen[:, 0] - cx, cen[:, 1] - cy) < rad
+    D = np.where(ins == inside_high, 1.0, 1.0 / contrast)
+    return xy, tri, D
+
+
 @dataclass
 class Request:
     rid: int
@@ -217,17 +225,16 @@ def serve_stream(seed: int = 3, nreq: int = 2000, rate: float = 200.0, K_lo: flo
         steps = int(rng.integers(steps_lo, steps_hi + 1))
         mesh_seed = int(rng.integers(0, 2 ** 31 - 1))
         check = bool(rng.uniform() < check_frac)
+        build = (lambda mm, ms, ccx, ccy, rr, ih, con: (lambda: _circle_mesh(mm, ms, ccx, ccy, rr, ih, con)))(
+            m, mesh_seed, cx, cy, rad, inside_high, contrast)
         if build_mesh:
-            xy, tri = unit_square_mesh(m, 0.1, mesh_seed)
-            cen = centroids(xy, tri)
-            ins = np.hypot(cen[:, 0] - cx, cen[:, 1] - cy) < rad
-            hi, lo = 1.0, 1.0 / contrast
-            D = np.where(ins == inside_high, hi, lo)
+            xy, tri, D = build()
         else:
             xy = tri = D = None
         w0 = 0.05 + 0.1 * rng.uniform()
         u0 = (lambda ccx, ccy, ww: (lambda x, y: np.exp(-((x - ccx) ** 2 + (y - ccy) ** 2) / ww ** 2)))(cx, cy, w0)
         wl = Workload("req%d_N%d_m%d" % (i, N, m), N, m, xy, tri, PERIODIC, D, (float(vx), float(vy)), u0, steps,
-                      dt=None, dt_factor=0.5, meta={"mesh_seed": mesh_seed, "contrast": contrast})
+                      dt=None, dt_factor=0.5, meta={"mesh_seed": mesh_seed, "contrast": contrast, "build": build,
+                                                    "triangles": 2 * m * m})
         reqs.append(Request(i, t, wl, check))
     return reqs
