@@ -125,6 +125,19 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def profiled_traffic(args):
+    """DRAM bytes (read + write) per launch of the stage kernel from the committed ncu
+    summary of this workload, or None for another workload."""
+    if args.m != 256 or args.rk_steps <= 0:
+        return None
+    import re
+    p = os.path.join(ROOT, "profiles", "stage_kernels_circle_pulse_N4_m256_fp32.md")
+    if not os.path.exists(p):
+        return None
+    m = re.search(r"traffic_bytes_per_launch edge_flux_kernel<float,4,1>: (\d+)", open(p).read())
+    return int(m.group(1)) if m else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -293,7 +306,8 @@ def run_ours(args):
     elem_avg = elem_ms / elem_n
     ach = edge_bytes / (edge_avg / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": "edge_flux_kernel<float,4,VOL=1>", "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+            "frac": ach / peak, "peak_source": peak_kind, "traffic": profiled_traffic(args),
+            "traffic_source": "profiles/stage_kernels_circle_pulse_N4_m256_fp32.md (ncu, one launch)",
             "alg_bytes_per_launch": edge_bytes, "avg_launch_us": edge_avg * 1e3,
             "share_of_kernel_time": edge_ms / (edge_ms + elem_ms),
             "elem_kernel": {"name": "elem_lite_kernel<float,4,MODE>", "alg_bytes_per_launch": elem_bytes,
