@@ -42,6 +42,7 @@ extern "C" {
 #endif
 
 typedef struct rdg_ctx rdg_ctx;
+typedef struct rdg_batch rdg_batch;
 
 enum {
   RDG_OK = 0,
@@ -168,8 +169,8 @@ int rdg_set_l2_resident_bytes(rdg_ctx* ctx, int64_t bytes);
 int rdg_profile(rdg_ctx* ctx, int enable);
 int rdg_kernel_stats(rdg_ctx* ctx, int64_t* launches, double* ms, int reset);
 
-/* Wait for the context's stream; returns RDG_ECUDA if device work failed and RDG_ETIMEOUT
- * if a kernel's bounded wait on its copy pipeline gave up (the error word is then cleared). */
+/* Wait for the context's stream; returns RDG_ECUDA if device work failed or a kernel's
+ * index self-check found a corrupt edge table (the device error word is then cleared). */
 int rdg_synchronize(rdg_ctx* ctx);
 
 /* Device bytes a context allocates for order N, nt triangles, n_edges edges (n_boundary of
@@ -188,6 +189,41 @@ int rdg_reference_operator(int N, int which, double* out);
  * double), plus per edge (k1, f1, k2, f2) into ids[n_edges][4] (k2 = -1-b for the b-th
  * boundary edge).  For checks and tooling; not needed for solving. */
 int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids);
+
+/* ---- Batched stepping of independent problems ------------------------------------------
+ * Many independent solves (different meshes, orders N = 1..6, precisions, dt) advanced
+ * together: every member is a context set up as for a single solve (mesh, operators,
+ * forcing, state); a batch step advances every member by the same number of SSP-RK3 steps
+ * (Sec. 2.1 time integration of each problem's semi-discrete system, each with its own dt).
+ * The members' kernels are captured as parallel branches of one CUDA graph of `chunk` steps
+ * and replayed with one launch per chunk, so problems of all sizes and orders run
+ * concurrently.  The paper solves one problem at a time and has no counterpart.
+ * Ownership: the batch borrows its member contexts; remove a member (or destroy the batch)
+ * before destroying the context.  Ordering: a batch step runs after the work already
+ * enqueued on every member's stream, and later work on a member's stream runs after it. */
+
+/* Create an empty batch on `device`.  cuda_stream: stream the graph is launched on (NULL: an
+ * own non-blocking stream).  chunk: steps per captured graph (1..1024).  RDG_EINVAL on a
+ * bad argument, RDG_ECUDA if stream/event creation fails. */
+int rdg_batch_create(rdg_batch** out, int device, void* cuda_stream, int chunk);
+/* Wait for the batch's work and free it (not the member contexts).  NULL is a no-op. */
+int rdg_batch_destroy(rdg_batch* b);
+/* Text of the batch's last error. */
+const char* rdg_batch_last_error(const rdg_batch* b);
+/* Add a context whose operators are set up: its resident state is stepped from time t0
+ * with step dt.  RDG_ESTATE without operators; RDG_EINVAL for another device, a
+ * non-positive dt, a non-finite t0, or a context already in the batch. */
+int rdg_batch_add(rdg_batch* b, rdg_ctx* ctx, double t0, double dt);
+/* Remove a member (waits for its branch); RDG_EINVAL if ctx is not a member. */
+int rdg_batch_remove(rdg_batch* b, rdg_ctx* ctx);
+/* Number of members into *n. */
+int rdg_batch_size(const rdg_batch* b, int* n);
+/* Enqueue nsteps SSP-RK3 steps of every member: floor(nsteps/chunk) replays of the graph
+ * (captured on first use after the membership changed) and the remainder as direct
+ * launches on the branch streams.  Each member continues from its own time. */
+int rdg_batch_step(rdg_batch* b, int64_t nsteps);
+/* Wait for the batch stream, then check every member as rdg_synchronize does. */
+int rdg_batch_synchronize(rdg_batch* b);
 
 #ifdef __cplusplus
 }

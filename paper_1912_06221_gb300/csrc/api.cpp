@@ -681,6 +681,21 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
+namespace rdg {
+
+int enqueue_rk_step_on(rdg_ctx* ctx, cudaStream_t s, const TimeArg& base, double dt) {
+  cudaStream_t saved = ctx->cap_stream;
+  const bool was = ctx->capturing;
+  ctx->cap_stream = s;
+  ctx->capturing = true;
+  int rc = enqueue_rk_step(ctx, base, dt);
+  ctx->cap_stream = saved;
+  ctx->capturing = was;
+  return rc;
+}
+
+}  // namespace rdg
+
 extern "C" {
 
 int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t) {

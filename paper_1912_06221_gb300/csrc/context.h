@@ -58,3 +58,8 @@ struct rdg_ctx {
   int g_chunk = 0;
 };
 
+namespace rdg {
+// One SSP-RK3 step of ctx's resident state with every launch on stream s (which may be
+// capturing); used by the batch, whose member steps run on per-member branch streams.
+int enqueue_rk_step_on(rdg_ctx* ctx, cudaStream_t s, const TimeArg& base, double dt);
+}  // namespace rdg

@@ -52,6 +52,14 @@ SIGNATURES = {
     "rdg_query_bytes": (_INT, [_INT, _I64, _I64, _I64, _INT, _INT, _INT, ctypes.POINTER(_I64)]),
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
     "rdg_get_edge_operators": (_INT, [_P, _P, _P]),
+    "rdg_batch_create": (_INT, [ctypes.POINTER(_P), _INT, _P, _INT]),
+    "rdg_batch_destroy": (_INT, [_P]),
+    "rdg_batch_last_error": (ctypes.c_char_p, [_P]),
+    "rdg_batch_add": (_INT, [_P, _P, _D, _D]),
+    "rdg_batch_remove": (_INT, [_P, _P]),
+    "rdg_batch_size": (_INT, [_P, ctypes.POINTER(_INT)]),
+    "rdg_batch_step": (_INT, [_P, _I64]),
+    "rdg_batch_synchronize": (_INT, [_P]),
 }
 
 _lib = None
@@ -120,13 +128,8 @@ class Solver:
         self.precision = precision
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.np_dtype = np.float64 if precision == FP64 else np.float32
-        if stream is None:
-            stream = torch.cuda.current_stream(device)
-        self.stream = stream
+        self.stream, handle = _stream_handle(torch, stream, device)
         ctx = _P()
-        handle = stream.cuda_stream
-        if handle == 0:
-            handle = 1      # torch's default stream is the legacy default stream (cudaStreamLegacy)
         _check(self.lib.rdg_create(ctypes.byref(ctx), device, _P(handle)))
         self.ctx = ctx
         xy = np.ascontiguousarray(xy, np.float64)
@@ -237,3 +240,67 @@ class Solver:
         ms = (_D * 2)()
         self._call("rdg_kernel_stats", n, ms, 1 if reset else 0)
         return {"edge": (n[0], ms[0]), "elem": (n[1], ms[1])}
+
+
+def _stream_handle(torch, stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    handle = stream.cuda_stream
+    # torch's default stream (handle 0) is the legacy default stream, cudaStreamLegacy
+    return stream, (handle if handle != 0 else 1)
+
+
+class Batch:
+    """Independent solves stepped together: each member is a :class:`Solver` with its own
+    mesh, order, precision and dt; :meth:`step` advances all of them by the same number of
+    SSP-RK3 steps with one CUDA-graph launch per chunk of steps."""
+
+    def __init__(self, device: int = 0, stream=None, chunk: int = 16):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = device
+        self.stream, handle = _stream_handle(torch, stream, device)
+        b = _P()
+        rc = self.lib.rdg_batch_create(ctypes.byref(b), device, _P(handle), int(chunk))
+        if rc != RDG_OK:
+            raise RdgError(rc, "rdg_batch_create failed")
+        self.b = b
+        self.members = []
+
+    def _call(self, name, *args):
+        rc = getattr(self.lib, name)(self.b, *args)
+        if rc != RDG_OK:
+            msg = self.lib.rdg_batch_last_error(self.b)
+            raise RdgError(rc, msg.decode() if msg else "")
+
+    def add(self, solver: "Solver", dt: float, t0: float = 0.0):
+        self._call("rdg_batch_add", solver.ctx, float(t0), float(dt))
+        self.members.append(solver)
+
+    def remove(self, solver: "Solver"):
+        self._call("rdg_batch_remove", solver.ctx)
+        self.members.remove(solver)
+
+    def __len__(self):
+        n = _INT(0)
+        self._call("rdg_batch_size", ctypes.byref(n))
+        return n.value
+
+    def step(self, nsteps: int):
+        self._call("rdg_batch_step", int(nsteps))
+
+    def synchronize(self):
+        self._call("rdg_batch_synchronize")
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.rdg_batch_destroy(self.b)
+            self.b = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
