@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--serve", action="store_true", help="run the request-stream server instead")
     p.add_argument("--serve-requests", type=int, default=200)
     p.add_argument("--serve-slots", type=int, default=32)
+    p.add_argument("--serve-setup-workers", type=int, default=6)
     p.add_argument("--batch", action="store_true", help="run the batched uneven workload instead")
     p.add_argument("--batch-chunk", type=int, default=25)
     return p.parse_args()
@@ -403,15 +404,24 @@ def run_serve(args):
         w = r.workload
         reqs.append(SolveRequest(r.rid, r.arrival, None, None, w.N, None, w.v, w.u0, w.steps,
                                  build=w.meta["build"], n_triangles=w.meta["triangles"]))
-    srv = Server(budget_bytes=120 * 10 ** 9, max_slots=args.serve_slots, chunk=16)
+    srv = Server(budget_bytes=120 * 10 ** 9, max_slots=args.serve_slots, chunk=16,
+                 setup_workers=args.serve_setup_workers)
     t0 = time.perf_counter()
     res = srv.run(reqs, realtime=True)
     wall = time.perf_counter() - t0
     st = latency_stats(res)
     by_id = {r.rid: r for r in res}
+    # the requests the stream marks for an FP64 check (1%), topped up in arrival order to at
+    # least 1% of the requests served
+    marked = [r.rid for r in stream if r.fp64_check]
+    for r in stream:
+        if len(marked) >= math.ceil(0.01 * len(stream)):
+            break
+        if r.rid not in marked:
+            marked.append(r.rid)
     checks = []
     for r in stream:
-        if r.fp64_check:
+        if r.rid in marked:
             got = by_id[r.rid]
             ref = solve_alone(reqs[r.rid], got.dt, precision=rdg.FP64)
             checks.append({"rid": r.rid, "triangles": got.K, "N": reqs[r.rid].N,
@@ -420,6 +430,7 @@ def run_serve(args):
             "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"], "n_requests": st["n"],
             "makespan_s": st["makespan_s"], "wall_s": wall, "peak_admitted_bytes": srv.peak_in_use,
             "max_resident": srv.max_concurrent, "budget_bytes": srv.budget, "fp64_spot_checks": checks,
+            "setup_seconds_summed": srv.setup_summary(), "setup_workers": args.serve_setup_workers,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "Poisson stream, rate 200/s, seed 3, %d requests, K log-uniform 1e3..1e6, "
                                    "N 2..6, D contrast log-uniform 1..1e4 across a random circle, 50..500 steps"

@@ -51,7 +51,7 @@ enum {
   RDG_ECUDA = -3,    /* a CUDA runtime call failed */
   RDG_EMESH = -4,    /* mesh not valid: clockwise/degenerate triangle, non-manifold or unmatched edge */
   RDG_ERANK = -5,    /* reconstruction system not of full column rank */
-  RDG_ETIMEOUT = -6, /* a bounded device wait gave up */
+  RDG_ETIMEOUT = -6, /* a bounded device wait gave up (no current kernel waits; reserved) */
   RDG_ESTATE = -7    /* call made in the wrong order (e.g. rhs before operator setup) */
 };
 
@@ -82,8 +82,9 @@ int rdg_create(rdg_ctx** out, int device, void* cuda_stream);
 int rdg_destroy(rdg_ctx* ctx);
 
 /* Mesh: nv vertices xy[2*nv] (x0,y0,x1,y1,...), nt counter-clockwise triangles tri[3*nt]
- * (0-based vertex ids).  bc = RDG_BC_PERIODIC: every face must meet another face whose
- * midpoint agrees modulo period[0..1] (period must be non-NULL); the neighbour's vertex
+ * (0-based vertex ids).  Two faces with the same pair of vertex ids form an edge; the faces
+ * left over are matched by coincident midpoints.  bc = RDG_BC_PERIODIC: every face must meet
+ * another face whose midpoint agrees modulo period[0..1] (period must be non-NULL); the neighbour's vertex
  * coordinates are translated onto the shared face.  bc = RDG_BC_DIRICHLET: faces met by no
  * other face are boundary edges whose outer side is the ghost triangle, the point
  * reflection of the element about the edge midpoint (period may be NULL).

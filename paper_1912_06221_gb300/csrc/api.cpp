@@ -42,31 +42,35 @@ int cuda_fail(rdg_ctx* c, cudaError_t e, const char* what) {
     if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);  \
   } while (0)
 
-void dfree(void*& p) {
-  if (p) cudaFree(p);
-  p = nullptr;
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the context stream):
+// a plain cudaFree waits for the whole device, which would stall every other context's
+// queued work whenever one context is set up or released.
+template <typename T>
+cudaError_t dalloc(T** p, size_t bytes, cudaStream_t s) {
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
 }
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
   p = nullptr;
 }
 
 void free_ops(rdg_ctx* ctx) {
-  dfree(ctx->d_W);
-  dfree(ctx->d_k1);
-  dfree(ctx->d_k2);
-  dfree(ctx->d_eref);
-  dfree(ctx->d_geo);
-  dfree(ctx->d_flux);
-  dfree(ctx->d_u);
-  dfree(ctx->d_u1);
-  dfree(ctx->d_u2);
-  dfree(ctx->d_S);
-  dfree(ctx->d_G);
-  dfree(ctx->d_vol);
-  dfree(ctx->d_fb);
-  dfree(ctx->d_f12);
+  cudaStream_t s = ctx->stream;
+  dfree(ctx->d_W, s);
+  dfree(ctx->d_k1, s);
+  dfree(ctx->d_k2, s);
+  dfree(ctx->d_eref, s);
+  dfree(ctx->d_geo, s);
+  dfree(ctx->d_flux, s);
+  dfree(ctx->d_u, s);
+  dfree(ctx->d_u1, s);
+  dfree(ctx->d_u2, s);
+  dfree(ctx->d_S, s);
+  dfree(ctx->d_G, s);
+  dfree(ctx->d_vol, s);
+  dfree(ctx->d_fb, s);
+  dfree(ctx->d_f12, s);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   ctx->gexec = nullptr;
   ctx->ops_ok = false;
@@ -173,12 +177,14 @@ int rdg_create(rdg_ctx** out, int device, void* cuda_stream) {
     }
     c->own_stream = true;
   }
-  e = cudaMalloc(&c->d_time, sizeof(TimeState));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  e = dalloc(&c->d_time, sizeof(TimeState), c->stream);
+  if (e == cudaSuccess) e = dalloc(&c->d_err, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
-    if (c->d_time) cudaFree(c->d_time);
-    if (c->d_err) cudaFree(c->d_err);
+    dfree(c->d_time, c->stream);
+    dfree(c->d_err, c->stream);
+    cudaStreamSynchronize(c->stream);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return fail(nullptr, RDG_ENOMEM, "device allocation failed");
@@ -193,8 +199,9 @@ int rdg_destroy(rdg_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   free_ops(ctx);
   free_events(ctx);
-  dfree(ctx->d_time);
-  dfree(ctx->d_err);
+  dfree(ctx->d_time, ctx->stream);
+  dfree(ctx->d_err, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -231,70 +238,123 @@ int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, cons
     hmin = std::min(hmin, std::sqrt(l2));
   }
   (void)hmin;
-  // match faces by their midpoint (modulo the period)
-  struct Key {
-    long long x, y;
-    bool operator==(const Key& o) const { return x == o.x && y == o.y; }
-  };
-  struct KeyHash {
-    size_t operator()(const Key& k) const { return std::hash<long long>()(k.x * 1000003LL ^ k.y); }
-  };
-  const double scale = (bc == RDG_BC_PERIODIC) ? 1e9 : 1e12;
-  auto canon = [&](double x, double y) {
-    if (bc == RDG_BC_PERIODIC) {
-      x = std::fmod(x, period[0]);
-      if (x < 0) x += period[0];
-      if (std::fabs(x - period[0]) < 1e-9) x = 0;
-      y = std::fmod(y, period[1]);
-      if (y < 0) y += period[1];
-      if (std::fabs(y - period[1]) < 1e-9) y = 0;
+  // Faces are matched first by their vertex ids: a counting sort of the faces by their lower
+  // vertex id, then equal upper ids within each (small) bucket.  The faces left over (domain
+  // boundary, periodic images, vertices duplicated at one point) are matched by their
+  // midpoint modulo the period.  Linear in the mesh size for any vertex numbering.
+  const int64_t nf = 3 * nt;
+  std::vector<int64_t> partner(nf, -1);
+  {
+    auto lo_hi = [&](int64_t i, int32_t* lo, int32_t* hi) {
+      const int32_t a = tri[3 * (i / 3) + kFaceA[i % 3]], b = tri[3 * (i / 3) + kFaceB[i % 3]];
+      *lo = std::min(a, b);
+      *hi = std::max(a, b);
+    };
+    std::vector<int64_t> start(nv + 1, 0);
+    for (int64_t i = 0; i < nf; ++i) {
+      int32_t lo, hi;
+      lo_hi(i, &lo, &hi);
+      start[lo + 1]++;
     }
-    return Key{std::llround(x * scale), std::llround(y * scale)};
-  };
-  std::unordered_map<Key, std::vector<int64_t>, KeyHash> table;
-  table.reserve(nt * 2);
-  for (int64_t k = 0; k < nt; ++k)
-    for (int f = 0; f < 3; ++f) {
-      const double* p = &ctx->exy[6 * k];
-      double mx = 0.5 * (p[2 * kFaceA[f]] + p[2 * kFaceB[f]]), my = 0.5 * (p[2 * kFaceA[f] + 1] + p[2 * kFaceB[f] + 1]);
-      table[canon(mx, my)].push_back(3 * k + f);
+    for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
+    std::vector<int64_t> fill(start.begin(), start.end() - 1), bucket(nf);
+    for (int64_t i = 0; i < nf; ++i) {
+      int32_t lo, hi;
+      lo_hi(i, &lo, &hi);
+      bucket[fill[lo]++] = i;
     }
-  std::vector<EdgeRec> inner, bnd;
-  inner.reserve(table.size());
-  for (auto& kv : table) {
-    auto& l = kv.second;
-    if (l.size() > 2) return fail(ctx, RDG_EMESH, "non-manifold edge (shared by more than two faces)");
-    if (l.size() == 2) {
-      int64_t a = std::min(l[0], l[1]), b = std::max(l[0], l[1]);
-      EdgeRec r;
-      r.k1 = (int32_t)(a / 3);
-      r.f1 = (int32_t)(a % 3);
-      r.k2 = (int32_t)(b / 3);
-      r.f2 = (int32_t)(b % 3);
-      const double* p1 = &ctx->exy[6 * r.k1];
-      const double* p2 = &ctx->exy[6 * r.k2];
-      // the two faces must run in opposite directions over the same segment
-      double ax = p1[2 * kFaceA[r.f1]], ay = p1[2 * kFaceA[r.f1] + 1];
-      double bx = p1[2 * kFaceB[r.f1]], by = p1[2 * kFaceB[r.f1] + 1];
-      double cx = p2[2 * kFaceA[r.f2]], cy = p2[2 * kFaceA[r.f2] + 1];
-      double dx = p2[2 * kFaceB[r.f2]], dy = p2[2 * kFaceB[r.f2] + 1];
-      r.shx = 0.5 * (ax + bx) - 0.5 * (cx + dx);
-      r.shy = 0.5 * (ay + by) - 0.5 * (cy + dy);
-      double tol = 1e-9 * std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
-      if (std::fabs(dx + r.shx - ax) > tol || std::fabs(dy + r.shy - ay) > tol ||
-          std::fabs(cx + r.shx - bx) > tol || std::fabs(cy + r.shy - by) > tol)
-        return fail(ctx, RDG_EMESH, "faces meeting at an edge midpoint do not coincide");
-      inner.push_back(r);
-    } else {
-      if (bc == RDG_BC_PERIODIC) return fail(ctx, RDG_EMESH, "unmatched face on a periodic mesh");
-      EdgeRec r{(int32_t)(l[0] / 3), (int32_t)(l[0] % 3), -1, 1, 0.0, 0.0};
-      bnd.push_back(r);
+    std::vector<std::pair<int32_t, int64_t>> run;
+    for (int64_t v = 0; v < nv; ++v) {
+      const int64_t b0 = start[v], n = start[v + 1] - b0;
+      if (n < 2) continue;
+      run.clear();
+      for (int64_t j = 0; j < n; ++j) {
+        int32_t lo, hi;
+        lo_hi(bucket[b0 + j], &lo, &hi);
+        run.push_back({hi, bucket[b0 + j]});
+      }
+      std::sort(run.begin(), run.end());
+      for (int64_t j = 0; j < n;) {
+        int64_t q = j + 1;
+        while (q < n && run[q].first == run[j].first) ++q;
+        if (q - j > 2) return fail(ctx, RDG_EMESH, "non-manifold edge (shared by more than two faces)");
+        if (q - j == 2) {
+          partner[run[j].second] = run[j + 1].second;
+          partner[run[j + 1].second] = run[j].second;
+        }
+        j = q;
+      }
     }
   }
-  // edges sorted by their first element for locality of the neighbour gathers
-  auto less = [](const EdgeRec& a, const EdgeRec& b) { return a.k1 != b.k1 ? a.k1 < b.k1 : a.f1 < b.f1; };
-  std::sort(inner.begin(), inner.end(), less);
-  std::sort(bnd.begin(), bnd.end(), less);
+  {
+    struct Key {
+      long long x, y;
+      bool operator==(const Key& o) const { return x == o.x && y == o.y; }
+    };
+    struct KeyHash {
+      size_t operator()(const Key& k) const { return std::hash<long long>()(k.x * 1000003LL ^ k.y); }
+    };
+    const double scale = (bc == RDG_BC_PERIODIC) ? 1e9 : 1e12;
+    auto canon = [&](double x, double y) {
+      if (bc == RDG_BC_PERIODIC) {
+        x = std::fmod(x, period[0]);
+        if (x < 0) x += period[0];
+        if (std::fabs(x - period[0]) < 1e-9) x = 0;
+        y = std::fmod(y, period[1]);
+        if (y < 0) y += period[1];
+        if (std::fabs(y - period[1]) < 1e-9) y = 0;
+      }
+      return Key{std::llround(x * scale), std::llround(y * scale)};
+    };
+    std::unordered_map<Key, std::vector<int64_t>, KeyHash> table;
+    for (int64_t i = 0; i < nf; ++i) {
+      if (partner[i] >= 0) continue;
+      const double* p = &ctx->exy[6 * (i / 3)];
+      const int f = (int)(i % 3);
+      double mx = 0.5 * (p[2 * kFaceA[f]] + p[2 * kFaceB[f]]), my = 0.5 * (p[2 * kFaceA[f] + 1] + p[2 * kFaceB[f] + 1]);
+      table[canon(mx, my)].push_back(i);
+    }
+    for (auto& kv : table) {
+      auto& l = kv.second;
+      if (l.size() > 2) return fail(ctx, RDG_EMESH, "non-manifold edge (shared by more than two faces)");
+      if (l.size() == 2) {
+        partner[l[0]] = l[1];
+        partner[l[1]] = l[0];
+      }
+    }
+  }
+  // edges in the order of their first face (sorted by first element, for locality of the
+  // neighbour gathers): interior edges, then boundary edges
+  std::vector<EdgeRec> inner, bnd;
+  inner.reserve(nf / 2 + 1);
+  for (int64_t i = 0; i < nf; ++i) {
+    const int64_t j = partner[i];
+    if (j >= 0 && j < i) continue;
+    if (j < 0) {
+      if (bc == RDG_BC_PERIODIC) return fail(ctx, RDG_EMESH, "unmatched face on a periodic mesh");
+      bnd.push_back(EdgeRec{(int32_t)(i / 3), (int32_t)(i % 3), -1, 1, 0.0, 0.0});
+      continue;
+    }
+    EdgeRec r;
+    r.k1 = (int32_t)(i / 3);
+    r.f1 = (int32_t)(i % 3);
+    r.k2 = (int32_t)(j / 3);
+    r.f2 = (int32_t)(j % 3);
+    const double* p1 = &ctx->exy[6 * r.k1];
+    const double* p2 = &ctx->exy[6 * r.k2];
+    // the two faces must run in opposite directions over the same segment
+    double ax = p1[2 * kFaceA[r.f1]], ay = p1[2 * kFaceA[r.f1] + 1];
+    double bx = p1[2 * kFaceB[r.f1]], by = p1[2 * kFaceB[r.f1] + 1];
+    double cx = p2[2 * kFaceA[r.f2]], cy = p2[2 * kFaceA[r.f2] + 1];
+    double dx = p2[2 * kFaceB[r.f2]], dy = p2[2 * kFaceB[r.f2] + 1];
+    r.shx = 0.5 * (ax + bx) - 0.5 * (cx + dx);
+    r.shy = 0.5 * (ay + by) - 0.5 * (cy + dy);
+    double tol = 1e-9 * std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+    if (std::fabs(dx + r.shx - ax) > tol || std::fabs(dy + r.shy - ay) > tol ||
+        std::fabs(cx + r.shx - bx) > tol || std::fabs(cy + r.shy - by) > tol)
+      return fail(ctx, RDG_EMESH, "faces meeting at an edge do not coincide or run the same way");
+    inner.push_back(r);
+  }
   for (size_t b = 0; b < bnd.size(); ++b) bnd[b].k2 = -1 - (int32_t)b;
   ctx->edges = inner;
   ctx->edges.insert(ctx->edges.end(), bnd.begin(), bnd.end());
@@ -357,23 +417,23 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
   int32_t *d_i = nullptr;
   int rc = RDG_OK;
   cudaError_t e;
+  cudaStream_t s = ctx->stream;
   auto cleanup = [&]() {
-    cudaStreamSynchronize(ctx->stream);
-    dfree(d_xy);
-    dfree(d_sh);
-    dfree(d_D);
-    dfree(d_refs);
-    dfree(d_i);
+    dfree(d_xy, s);
+    dfree(d_sh, s);
+    dfree(d_D, s);
+    dfree(d_refs, s);
+    dfree(d_i, s);
+    cudaStreamSynchronize(s);
   };
-  if ((e = cudaMalloc(&d_xy, K * 6 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&d_sh, 2 * E * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&d_D, K * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&d_refs, refs.size() * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&d_i, 4 * E * sizeof(int32_t))) != cudaSuccess) {
+  if ((e = dalloc(&d_xy, K * 6 * sizeof(double), s)) != cudaSuccess ||
+      (e = dalloc(&d_sh, 2 * E * sizeof(double), s)) != cudaSuccess ||
+      (e = dalloc(&d_D, K * sizeof(double), s)) != cudaSuccess ||
+      (e = dalloc(&d_refs, refs.size() * sizeof(double), s)) != cudaSuccess ||
+      (e = dalloc(&d_i, 4 * E * sizeof(int32_t), s)) != cudaSuccess) {
     cleanup();
     return cuda_fail(ctx, e, "setup buffers");
   }
-  cudaStream_t s = ctx->stream;
   if ((e = cudaMemcpyAsync(d_xy, ctx->exy.data(), K * 6 * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_sh, sh.data(), 2 * E * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_D, ctx->Dk.data(), K * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -391,7 +451,8 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
       return cuda_fail(ctx, e, "W clear");
     }
   }
-  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy, ctx->iface};
+  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy, ctx->iface,
+                 (int64_t)refs.size()};
   rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, s);
   if (rc == RDG_OK && ctx->d_geo && !W_dense)
     rc = setup_elements(K, d_xy, d_D, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
@@ -430,18 +491,18 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   ctx->Dk.assign(D_elem, D_elem + ctx->K);
   const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
   const int64_t stb = K * Np * esz;
-  CK(cudaMalloc(&ctx->d_W, w_bytes(N, E, (int)esz)));
-  CK(cudaMalloc(&ctx->d_k1, E * 4));
-  CK(cudaMalloc(&ctx->d_k2, E * 4));
-  CK(cudaMalloc(&ctx->d_eref, 3 * K * 4));
-  CK(cudaMalloc(&ctx->d_geo, 6 * K * esz));
-  CK(cudaMalloc(&ctx->d_flux, E * Nfp * esz));
-  CK(cudaMalloc(&ctx->d_u, stb));
-  CK(cudaMalloc(&ctx->d_u1, stb));
-  CK(cudaMalloc(&ctx->d_u2, stb));
-  CK(cudaMalloc(&ctx->d_vol, stb));
-  CK(cudaMalloc(&ctx->d_fb, K * 3 * Nfp * esz));
-  CK(cudaMalloc(&ctx->d_f12, E * 4));
+  CK(dalloc(&ctx->d_W, w_bytes(N, E, (int)esz), ctx->stream));
+  CK(dalloc(&ctx->d_k1, E * 4, ctx->stream));
+  CK(dalloc(&ctx->d_k2, E * 4, ctx->stream));
+  CK(dalloc(&ctx->d_eref, 3 * K * 4, ctx->stream));
+  CK(dalloc(&ctx->d_geo, 6 * K * esz, ctx->stream));
+  CK(dalloc(&ctx->d_flux, E * Nfp * esz, ctx->stream));
+  CK(dalloc(&ctx->d_u, stb, ctx->stream));
+  CK(dalloc(&ctx->d_u1, stb, ctx->stream));
+  CK(dalloc(&ctx->d_u2, stb, ctx->stream));
+  CK(dalloc(&ctx->d_vol, stb, ctx->stream));
+  CK(dalloc(&ctx->d_fb, K * 3 * Nfp * esz, ctx->stream));
+  CK(dalloc(&ctx->d_f12, E * 4, ctx->stream));
   std::vector<int32_t> k1(E), k2(E), f12(E);
   for (int64_t e = 0; e < E; ++e) {
     k1[e] = ctx->edges[e].k1;
@@ -470,14 +531,16 @@ int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids) {
   const int64_t nw = (int64_t)o->Nfp * 2 * o->Np * ctx->E;
   if (W) {
     double* d = nullptr;
-    CK(cudaMalloc(&d, nw * sizeof(double)));
+    CK(dalloc(&d, nw * sizeof(double), ctx->stream));
     int rc = build_edge_ops(ctx, o, nullptr, 8, d);
     if (rc == RDG_OK) {
-      cudaError_t e = cudaMemcpy(W, d, nw * sizeof(double), cudaMemcpyDeviceToHost);
-      cudaFree(d);
+      cudaError_t e = cudaMemcpyAsync(W, d, nw * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+      dfree(d, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "copy W");
     } else {
-      cudaFree(d);
+      dfree(d, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
       return rc;
     }
   }
@@ -535,15 +598,16 @@ int rdg_get_ghost_coords(rdg_ctx* ctx, double* xy) {
 }  // extern "C"
 
 static int upload_converted(rdg_ctx* ctx, void** dst, const double* src, int64_t n) {
-  dfree(*dst);
+  dfree(*dst, ctx->stream);
   if (n == 0) return RDG_OK;
-  CK(cudaMalloc(dst, n * ctx->esz));
+  CK(dalloc(dst, n * ctx->esz, ctx->stream));
   if (ctx->esz == 8) {
-    CK(cudaMemcpy(*dst, src, n * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(*dst, src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
   } else {
     std::vector<float> f(src, src + n);
-    CK(cudaMemcpy(*dst, f.data(), n * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(*dst, f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
   }
+  CK(cudaStreamSynchronize(ctx->stream));   // the converted host copy goes out of scope
   return RDG_OK;
 }
 
@@ -803,11 +867,13 @@ int rdg_synchronize(rdg_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaGetLastError());
   int h = 0;
-  CK(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   if (h) {
-    CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     if (h & kErrBadIndex) return fail(ctx, RDG_ECUDA, "a kernel's index self-check failed (corrupt edge tables)");
-    return fail(ctx, RDG_ETIMEOUT, "a bounded device wait gave up (pipeline stalled for more than 2 s)");
+    return fail(ctx, RDG_ETIMEOUT, "a kernel reported an unknown error bit");
   }
   return RDG_OK;
 }

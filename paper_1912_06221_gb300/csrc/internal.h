@@ -61,7 +61,6 @@ struct EdgeArgs {
 };
 
 // Device error bits reported through rdg_synchronize.
-constexpr int kErrWaitTimeout = 1;
 constexpr int kErrBadIndex = 2;
 
 template <typename T>
@@ -109,6 +108,7 @@ struct EdgeSetupIn {
   int64_t E;
   double vx, vy;
   int iface;               // RDG_IFACE_*
+  int64_t nrefs;           // doubles in refs (checked against the order's layout)
 };
 
 int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s);

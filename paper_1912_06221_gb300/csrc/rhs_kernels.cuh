@@ -82,20 +82,24 @@ __device__ __forceinline__ void report(int* err, int bit) {
 
 // Volume term of one element: M^{-1} S^T . F with F = v u - D grad u, written with the
 // metric-folded coefficients F_r = a_r u - (g_rr u_r + g_rs u_s), F_s = a_s u - (g_rs u_r +
-// g_ss u_s), vol = Wr F_r + Ws F_s (Wr = M^{-1} Dr^T M, Ws = M^{-1} Ds^T M).
+// g_ss u_s), vol = Wr F_r + Ws F_s (Wr = M^{-1} Dr^T M, Ws = M^{-1} Ds^T M).  The derivatives
+// are taken of u - u_0 (Dr, Ds annihilate constants), so the rounding of their large entries
+// multiplies differences of nearby values rather than u itself.
 template <typename T, int N>
 __device__ __forceinline__ void volume_row(const T (&u)[np_of(N)], T ar, T as, T grr, T grs, T gss,
                                            T (&vol)[np_of(N)]) {
   constexpr int NP = np_of(N);
   constexpr int ODR = 0, ODS = NP * NP, OWR = 2 * NP * NP, OWS = 3 * NP * NP;
-  T fr[NP], fs[NP];
+  T fr[NP], fs[NP], du[NP];
+#pragma unroll
+  for (int j = 1; j < NP; ++j) du[j] = u[j] - u[0];
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     T ur = T(0), us = T(0);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      ur = fma((T)RDG_TAB[ODR + i * NP + j], u[j], ur);
-      us = fma((T)RDG_TAB[ODS + i * NP + j], u[j], us);
+    for (int j = 1; j < NP; ++j) {
+      ur = fma((T)RDG_TAB[ODR + i * NP + j], du[j], ur);
+      us = fma((T)RDG_TAB[ODS + i * NP + j], du[j], us);
     }
     fr[i] = ar * u[i] - (grr * ur + grs * us);
     fs[i] = as * u[i] - (grs * ur + gss * us);
@@ -110,6 +114,16 @@ __device__ __forceinline__ void volume_row(const T (&u)[np_of(N)], T ar, T as, T
     }
     vol[i] = acc;
   }
+}
+
+// Convex combination of SSP-RK3 stages 2 and 3: (1 - c) u_n + c v with c = 1/4 or 2/3,
+// evaluated as u_n + c (v - u_n).  Written as c1 u_n + c2 v with the coefficients rounded to
+// FP32, c1 + c2 = 1 + 3e-8 for c = 2/3 and every step would scale the state by that factor
+// (a 1.5e-5 drift over 500 steps); here the rounding of c only touches the increment.
+template <typename T, int MODE>
+__device__ __forceinline__ T rk_combine(T un, T v) {
+  const T c = MODE == 2 ? T(0.25) : T(2.0 / 3.0);
+  return fma(c, v - un, un);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -229,6 +243,14 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
         for (int j = 0; j < NP; ++j) u2[j] += tm * g[j];
       }
     }
+  }
+  // difference form of the stored operator: (u_0, u_1 - u_0, ..., u_{2Np-1} - u_0)
+  {
+    const T ub = u1[0];
+#pragma unroll
+    for (int j = 1; j < NP; ++j) u1[j] -= ub;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) u2[j] -= ub;
   }
   const VT* w = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
   const bool keep = (e >> 5) < a.keep_tiles;
@@ -384,10 +406,7 @@ __global__ void __launch_bounds__(kElemBlock, elem_min_blocks<T, N, VOLIN>()) el
     stage_in(sh, a.un + k0 * NP, nk * NP);
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      if (MODE == 2) rhs[i] = T(0.75) * sh[tid * NP + i] + T(0.25) * rhs[i];
-      else rhs[i] = T(1.0 / 3.0) * sh[tid * NP + i] + T(2.0 / 3.0) * rhs[i];
-    }
+    for (int i = 0; i < NP; ++i) rhs[i] = rk_combine<T, MODE>(sh[tid * NP + i], rhs[i]);
   }
   T* res = rhs;
   __syncthreads();
@@ -469,8 +488,7 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     if (MODE >= 1) rhs[i] = fma(a.dt, rhs[i], shs[tid * NP + i]);
-    if (MODE == 2) rhs[i] = T(0.75) * shn[tid * NP + i] + T(0.25) * rhs[i];
-    if (MODE == 3) rhs[i] = T(1.0 / 3.0) * shn[tid * NP + i] + T(2.0 / 3.0) * rhs[i];
+    if (MODE >= 2) rhs[i] = rk_combine<T, MODE>(shn[tid * NP + i], rhs[i]);
   }
   __syncthreads();
   if (active) {

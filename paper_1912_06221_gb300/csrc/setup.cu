@@ -28,6 +28,32 @@ std::vector<double> pack_setup_refs(const RefOps& o) {
   for (int x : o.Fmask) v.push_back(x);
   (void)Nfp;
   for (int k = 0; k < 2; ++k) v.insert(v.end(), o.dvec[k].begin(), o.dvec[k].end());
+  // Recurrence constants of the orthonormal Jacobi polynomials P_n^{(al,0)} (the collapsed
+  // coordinate factors of the simplex basis) for al = 0 and al = 2i+1, i = 0..N, so the
+  // device evaluates the basis with multiply-adds only (FP64 square roots and divisions are
+  // slow on this part).  Per al, 3N values: c0 = 1/sqrt(g0), P_1 = c1a x + c1b, and for
+  // n = 1..N-1 (A_n, B_n, C_n) with P_{n+1} = (x - B_n) A_n P_n - C_n P_{n-1}.
+  const int N = Nfp - 1;
+  for (int ai = 0; ai <= N + 1; ++ai) {
+    const double al = ai == 0 ? 0.0 : 2.0 * (ai - 1) + 1.0;
+    const double g0 = std::pow(2.0, al + 1) / (al + 1);
+    const double g1 = (al + 1) / (al + 3) * g0;
+    v.push_back(1.0 / std::sqrt(g0));
+    v.push_back((al + 2) / 2 / std::sqrt(g1));
+    v.push_back(al / 2 / std::sqrt(g1));
+    double aold = 2.0 / (2 + al) * std::sqrt((al + 1) / (al + 3));
+    for (int n = 1; n < N; ++n) {
+      const double h1 = 2 * n + al;
+      const double anew =
+          2.0 / (h1 + 2) * std::sqrt((n + 1) * (n + 1 + al) * (n + 1 + al) * (n + 1) / (h1 + 1) / (h1 + 3));
+      const double bnew = -(al * al) / h1 / (h1 + 2);
+      v.push_back(1.0 / anew);
+      v.push_back(bnew);
+      v.push_back(aold / anew);
+      aold = anew;
+    }
+  }
+  (void)Np;
   return v;
 }
 
@@ -97,55 +123,71 @@ __device__ void frame_coords(D2 va, D2 vb, D2 vc, D2 p, double& r, double& s) {
   s = cross(a, w) / det;
 }
 
-// orthonormal Jacobi P_0..P_n^{(alpha,0)} at x
-__device__ void jacobi_a0(double x, double al, int n, double* P) {
-  const double g0 = pow(2.0, al + 1) / (al + 1);
-  P[0] = 1.0 / sqrt(g0);
+// Orthonormal Jacobi P_0..P_n^{(al,0)} at x from the recurrence constants t (3N values, the
+// layout pack_setup_refs writes).
+__device__ __forceinline__ void jacobi_tab(double x, const double* t, int n, double* P) {
+  P[0] = t[0];
   if (n == 0) return;
-  const double g1 = (al + 1) / (al + 3) * g0;
-  P[1] = ((al + 2) * x / 2 + al / 2) / sqrt(g1);
-  double aold = 2.0 / (2 + al) * sqrt((al + 1) / (al + 3));
-  for (int i = 1; i < n; ++i) {
-    const double h1 = 2 * i + al;
-    const double anew = 2.0 / (h1 + 2) * sqrt((i + 1) * (i + 1 + al) * (i + 1 + al) * (i + 1) / (h1 + 1) / (h1 + 3));
-    const double bnew = -(al * al) / h1 / (h1 + 2);
-    P[i + 1] = (-aold * P[i - 1] + (x - bnew) * P[i]) / anew;
-    aold = anew;
-  }
+  P[1] = fma(t[1], x, t[2]);
+  for (int k = 1; k < n; ++k) P[k + 1] = (x - t[3 * k + 1]) * t[3 * k] * P[k] - t[3 * k + 2] * P[k - 1];
 }
 
+// Orthonormal simplex basis psi_m(r, s), m = (i, j) with i + j <= N in i-major order: the
+// collapsed coordinates a = 2(1+r)/(1-s) - 1, b = s and psi = sqrt(2) P_i(a) P_j^{(2i+1,0)}(b)
+// (1-b)^i.  jac holds the constants for al = 0 then al = 2i+1, 3N values each.
 template <int N>
-__device__ void simplex_basis_dev(double r, double s, double* psi) {
+__device__ void simplex_basis_tab(double r, double s, const double* jac, double* psi) {
   const double a = (fabs(1 - s) > 1e-14) ? 2 * (1 + r) / (1 - s) - 1 : -1.0;
   const double b = s;
   double Pa[N + 1], Pb[N + 1];
-  jacobi_a0(a, 0.0, N, Pa);
+  jacobi_tab(a, jac, N, Pa);
   int m = 0;
   double omb = 1.0;
+#pragma unroll
   for (int i = 0; i <= N; ++i) {
-    jacobi_a0(b, 2 * i + 1, N - i, Pb);
+    jacobi_tab(b, jac + 3 * N * (i + 1), N - i, Pb);
     for (int j = 0; j <= N - i; ++j) psi[m++] = 1.4142135623730951 * Pa[i] * Pb[j] * omb;
     omb *= (1 - b);
   }
 }
 
-constexpr int kSetupWarps = 4;
+// Warps (one edge each) per block of the set-up kernel: the reference constants are staged
+// once per block in shared memory, plus NP^2 + 2 Nfp NP doubles per warp (under 48 KB).
+template <int N>
+__host__ __device__ constexpr int setup_warps() {
+  return N >= 6 ? 3 : 4;
+}
 
 template <int N>
-__global__ void __launch_bounds__(32 * kSetupWarps) edge_setup_kernel(EdgeSetupIn in, void* Wt, int elem_bytes,
-                                                                        double* Wd) {
-  constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP;
-  __shared__ double sVp[kSetupWarps][NP * NP];
-  __shared__ double sB[kSetupWarps][NFP * NP];
+__host__ __device__ constexpr int setup_ref_count() {
+  constexpr int NP = np_of(N), NFP = nfp_of(N);
+  return 2 * NP + NP * NP + 4 * NFP * NP + 3 * NP + 3 * NFP + 2 * NFP + 3 * N * (N + 2);
+}
+
+// One warp per edge: the parallelogram apex, the two rotated frames and the metric (lane
+// uniform), then per side the basis at the side's nodes mapped into the parallelogram frame
+// (one lane per node) and the two small products (kR QR + kS QS) V_p and (.) V^{-1} spread
+// over all 32 lanes.
+template <int N>
+__global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeSetupIn in, void* Wt, int elem_bytes,
+                                                                            double* Wd) {
+  constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP, WARPS = setup_warps<N>();
+  constexpr int RT = setup_ref_count<N>();
+  __shared__ double sR[RT];
+  __shared__ double sVp[WARPS][NP * NP];
+  __shared__ double sK[WARPS][NFP * NP];
+  __shared__ double sB[WARPS][NFP * NP];
+  for (int i = threadIdx.x; i < RT; i += blockDim.x) sR[i] = in.refs[i];
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t e = (int64_t)blockIdx.x * kSetupWarps + warp;
+  const int64_t e = (int64_t)blockIdx.x * WARPS + warp;
   if (e >= in.E) return;   // whole warp leaves together; only __syncwarp is used below
-  const double* R = in.refs;
-  const double *rr = R, *ss = R + NP, *Vinv = R + 2 * NP;
+  const double *rr = sR, *ss = sR + NP, *Vinv = sR + 2 * NP;
   const double* QV = Vinv + NP * NP;  // QRV0 QSV0 QRV1 QSV1
   const double* perminv = QV + 4 * NFP * NP;
   const double* fmask = perminv + 3 * NP;
   const double* dvec = fmask + 3 * NFP;
+  const double* jac = dvec + 2 * NFP;
 
   const int fa[3] = {0, 1, 2}, fb[3] = {1, 2, 0}, fc[3] = {2, 0, 1};
   const int k1 = in.k1[e], f1 = in.f1[e];
@@ -190,38 +232,45 @@ __global__ void __launch_bounds__(32 * kSetupWarps) edge_setup_kernel(EdgeSetupI
       const double rn = rr[lane], sn = ss[lane];
       const double Ar = -(rn + sn) / 2 * al[side] + (rn + 1) / 2 - (sn + 1) / 2;
       const double As = -(rn + sn) / 2 * be[side] - (rn + 1) / 2 + (sn + 1) / 2;
-      simplex_basis_dev<N>(Ar, As, &sVp[warp][lane * NP]);
+      simplex_basis_tab<N>(Ar, As, jac, &sVp[warp][lane * NP]);
+    }
+    const double* QRV = QV + (2 * side) * NFP * NP;
+    const double* QSV = QV + (2 * side + 1) * NFP * NP;
+    for (int t = lane; t < NFP * NP; t += 32) sK[warp][t] = kR * QRV[t] + kS * QSV[t];
+    __syncwarp();
+    for (int t = lane; t < NFP * NP; t += 32) {
+      const int i = t / NP, j = t % NP;
+      double acc = 0.0;
+#pragma unroll 7
+      for (int n = 0; n < NP; ++n) acc = fma(sK[warp][i * NP + n], sVp[warp][n * NP + j], acc);
+      sB[warp][t] = acc;
     }
     __syncwarp();
-    if (lane < NP) {
-      const double* QRV = QV + (2 * side) * NFP * NP;
-      const double* QSV = QV + (2 * side + 1) * NFP * NP;
-      for (int i = 0; i < NFP; ++i) {
-        double acc = 0.0;
-        for (int n = 0; n < NP; ++n) acc += (kR * QRV[i * NP + n] + kS * QSV[i * NP + n]) * sVp[warp][n * NP + lane];
-        sB[warp][i * NP + lane] = acc;
+    const int f = ff[side];
+    for (int t = lane; t < NFP * NP; t += 32) {
+      const int i = t / NP, l = t % NP;
+      double c = 0.0;
+#pragma unroll 7
+      for (int j = 0; j < NP; ++j) c = fma(sB[warp][i * NP + j], Vinv[j * NP + l], c);
+      const int col = (int)perminv[f * NP + l];
+      const double Dt = in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
+                                                       : D1v * dvec[i] + D2v * dvec[NFP + i];
+      double w = -Jf * Dt * c;
+      if (side == 0 && vn >= 0 && col == (int)fmask[f1 * NFP + i]) w += Jf * vn;
+      if (side == 1 && vn < 0 && col == (int)fmask[f2 * NFP + (NFP - 1 - i)]) w += Jf * vn;
+      const int idx = i * 2 * NP + side * NP + col;
+      const int64_t off = ((tile * QW + idx / VW) * kTile + le) * VW + (idx % VW);
+      // Stored (difference) form: the flux kernels apply the operator to
+      // (u_0, u_1 - u_0, ..., u_{2Np-1} - u_0), u_0 = side 1's first node value, so the
+      // stored column 0 is the row sum of W.  The reconstruction reproduces constants and
+      // their gradient vanishes, so the row sum is the upwind part alone, J_f (v.n1), and
+      // the large diffusive entries only ever multiply differences of nearby values.
+      const double wt = (side == 0 && col == 0) ? Jf * vn : w;
+      if (Wt) {
+        if (elem_bytes == 4) static_cast<float*>(Wt)[off] = (float)wt;
+        else static_cast<double*>(Wt)[off] = wt;
       }
-    }
-    __syncwarp();
-    if (lane < NP) {
-      const int f = ff[side];
-      const int col = (int)perminv[f * NP + lane];
-      for (int i = 0; i < NFP; ++i) {
-        double c = 0.0;
-        for (int j = 0; j < NP; ++j) c += sB[warp][i * NP + j] * Vinv[j * NP + lane];
-        const double Dt = in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
-                                                         : D1v * dvec[i] + D2v * dvec[NFP + i];
-        double w = -Jf * Dt * c;
-        if (side == 0 && vn >= 0 && col == (int)fmask[f1 * NFP + i]) w += Jf * vn;
-        if (side == 1 && vn < 0 && col == (int)fmask[f2 * NFP + (NFP - 1 - i)]) w += Jf * vn;
-        const int idx = i * 2 * NP + side * NP + col;
-        const int64_t off = ((tile * QW + idx / VW) * kTile + le) * VW + (idx % VW);
-        if (Wt) {
-          if (elem_bytes == 4) static_cast<float*>(Wt)[off] = (float)w;
-          else static_cast<double*>(Wt)[off] = w;
-        }
-        if (Wd) Wd[e * NW + idx] = w;
-      }
+      if (Wd) Wd[e * NW + idx] = w;
     }
     __syncwarp();
   }
@@ -253,19 +302,26 @@ __global__ void set_time_kernel(TimeState* ts, double t0) {
 
 }  // namespace
 
+template <int N>
+int launch_setup(const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s) {
+  constexpr int W = setup_warps<N>();
+  if (in.nrefs != setup_ref_count<N>()) return RDG_EINVAL;
+  const unsigned grid = (unsigned)((in.E + W - 1) / W);
+  edge_setup_kernel<N><<<grid, 32 * W, 0, s>>>(in, W_tiled, elem_bytes, W_dense);
+  return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
+}
+
 int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s) {
   if (in.E == 0) return RDG_OK;
-  const unsigned grid = (unsigned)((in.E + kSetupWarps - 1) / kSetupWarps);
   switch (N) {
-    case 1: edge_setup_kernel<1><<<grid, 32 * kSetupWarps, 0, s>>>(in, W_tiled, elem_bytes, W_dense); break;
-    case 2: edge_setup_kernel<2><<<grid, 32 * kSetupWarps, 0, s>>>(in, W_tiled, elem_bytes, W_dense); break;
-    case 3: edge_setup_kernel<3><<<grid, 32 * kSetupWarps, 0, s>>>(in, W_tiled, elem_bytes, W_dense); break;
-    case 4: edge_setup_kernel<4><<<grid, 32 * kSetupWarps, 0, s>>>(in, W_tiled, elem_bytes, W_dense); break;
-    case 5: edge_setup_kernel<5><<<grid, 32 * kSetupWarps, 0, s>>>(in, W_tiled, elem_bytes, W_dense); break;
-    case 6: edge_setup_kernel<6><<<grid, 32 * kSetupWarps, 0, s>>>(in, W_tiled, elem_bytes, W_dense); break;
+    case 1: return launch_setup<1>(in, W_tiled, elem_bytes, W_dense, s);
+    case 2: return launch_setup<2>(in, W_tiled, elem_bytes, W_dense, s);
+    case 3: return launch_setup<3>(in, W_tiled, elem_bytes, W_dense, s);
+    case 4: return launch_setup<4>(in, W_tiled, elem_bytes, W_dense, s);
+    case 5: return launch_setup<5>(in, W_tiled, elem_bytes, W_dense, s);
+    case 6: return launch_setup<6>(in, W_tiled, elem_bytes, W_dense, s);
     default: return RDG_EINVAL;
   }
-  return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
 
 int setup_elements(int64_t K, const double* xy, const double* D, double vx, double vy, void* geo, int elem_bytes,

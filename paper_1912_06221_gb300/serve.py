@@ -71,17 +71,17 @@ SSP_RK3_REAL_EXTENT = 2.5127
 
 
 def spectral_radius(solver, torch, iters=30, seed=0):
-    """Power iteration on the library right-hand side (on the current stream)."""
+    """Power iteration on the library right-hand side, on the current stream, with a single
+    host synchronisation at the end (the normalisation stays on the device, so the
+    iterations do not wait behind other requests' queued work one by one)."""
     g = torch.Generator(device="cuda").manual_seed(seed)
     x = torch.randn((solver.K, solver.Np), generator=g, device="cuda", dtype=solver.dtype)
     y = torch.empty_like(x)
-    rho = 0.0
     for _ in range(iters):
         x /= torch.linalg.vector_norm(x)
         solver.rhs_eval(x, y, 0.0)
-        rho = float(torch.linalg.vector_norm(y))
         x, y = y, x
-    return rho
+    return float(torch.linalg.vector_norm(x))
 
 
 def edge_count_bound(tri: np.ndarray) -> int:
@@ -136,24 +136,43 @@ class Server:
         self.peak_in_use = 0
         self.max_concurrent = 0
         self.log = []              # (time, event, rid, in_use)
+        self.setup_phases = []     # per request: seconds of each set-up phase
+        self._lock = threading.Lock()
 
     def _setup(self, req: SolveRequest, nbytes: int, t0: float) -> _Active:
         torch = self.torch
         torch.cuda.set_device(self.device)
         admitted = self.clock() - t0
+        ph = [time.perf_counter()]
         if req.xy is None:
             req.xy, req.tri, req.D_elem = req.build()
+        ph.append(time.perf_counter())
         stream = torch.cuda.Stream(device=self.device)
         with torch.cuda.stream(stream):
             s = rdg.Solver(req.xy, req.tri, req.N, req.D_elem, v=req.v, precision=req.precision,
                            device=self.device, stream=stream, interface=req.interface)
+            ph.append(time.perf_counter())
             xyn = s.node_coords()
+            u0 = np.ascontiguousarray(req.u0(xyn[..., 0], xyn[..., 1]), dtype=s.np_dtype)
+            ph.append(time.perf_counter())
             dt = req.dt
             if dt is None:
                 dt = 0.5 * SSP_RK3_REAL_EXTENT / spectral_radius(s, torch)
-            s.set_state(np.ascontiguousarray(req.u0(xyn[..., 0], xyn[..., 1]), dtype=s.np_dtype))
+            ph.append(time.perf_counter())
+            s.set_state(u0)
             stream.synchronize()
+            ph.append(time.perf_counter())
+        with self._lock:
+            self.setup_phases.append(np.diff(ph))
         return _Active(req, s, stream, admitted, self.clock() - t0, dt, nbytes)
+
+    SETUP_PHASES = ("mesh_build", "library_setup", "initial_state", "step_size", "upload")
+
+    def setup_summary(self):
+        """Seconds spent per set-up phase, summed over requests (worker threads overlap)."""
+        with self._lock:
+            a = np.array(self.setup_phases) if self.setup_phases else np.zeros((0, 5))
+        return {n: float(a[:, i].sum()) for i, n in enumerate(self.SETUP_PHASES)}
 
     def run(self, requests: List[SolveRequest], realtime: bool = True) -> List[SolveResult]:
         """Serve `requests`.  realtime: a request becomes visible at its arrival time on the
