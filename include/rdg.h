@@ -21,7 +21,7 @@
  *    row (for i = 0..N, for j = 0..N-i); element vertex k maps to v_k through the affine map
  *    x = -(r+s)/2 x1 + (r+1)/2 x2 + (s+1)/2 x3 (Eq. mapping_tri).
  *  - nodal arrays are row-major [K][Np] (element-major), in the precision chosen at
- *    rdg_operator_setup (double for RDG_FP64, float for RDG_FP32).
+ *    rdg_operator_setup (double for RDG_FP64, float for RDG_FP32 and RDG_FP32_3XTF32).
  *  - triangles must be counter-clockwise; faces are (x1,x2), (x2,x3), (x3,x1).
  *
  * Status: every call returns 0 (RDG_OK) or a negative RDG_E* code; rdg_last_error() gives a
@@ -51,12 +51,16 @@ enum {
   RDG_ECUDA = -3,    /* a CUDA runtime call failed */
   RDG_EMESH = -4,    /* mesh not valid: clockwise/degenerate triangle, non-manifold or unmatched edge */
   RDG_ERANK = -5,    /* reconstruction system not of full column rank */
-  RDG_ETIMEOUT = -6, /* a bounded device wait gave up (no current kernel waits; reserved) */
+  RDG_ETIMEOUT = -6, /* a bounded device wait (for the tensor core, 1 s) gave up */
   RDG_ESTATE = -7    /* call made in the wrong order (e.g. rhs before operator setup) */
 };
 
 enum { RDG_BC_PERIODIC = 0, RDG_BC_DIRICHLET = 1 };
-enum { RDG_FP64 = 0, RDG_FP32 = 1 };
+/* Precision of the state and the hot path.  RDG_FP32_3XTF32: FP32 state with the edge flux in
+ * its GEMM form on the tensor cores (split 3xTF32 products against shared reference
+ * matrices, per-edge parameters instead of stored operators, see rdg_operator_setup); orders
+ * N = 1..5 (N = 6 runs the RDG_FP32 path). */
+enum { RDG_FP64 = 0, RDG_FP32 = 1, RDG_FP32_3XTF32 = 2 };
 enum { RDG_TAU_CONST = 0, RDG_TAU_COS = 1, RDG_TAU_SIN = 2 };
 /* Edge diffusion coefficient for element-wise D: the paper's Algorithm 2 (D~ = RDG(D1, D2)
  * on the diagonal) or the harmonic mean 2 D1 D2 / (D1 + D2) (not in the paper: stable for
@@ -94,13 +98,17 @@ int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, cons
                     int32_t bc, const double* period);
 
 /* Operators for order N (1..6) with element-wise diffusion D_elem[nt] (> 0), constant
- * velocity (vx, vy), arithmetic precision RDG_FP64 or RDG_FP32, interface rule
+ * velocity (vx, vy), arithmetic precision RDG_FP64, RDG_FP32 or RDG_FP32_3XTF32, interface rule
  * RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC for the edge diffusion coefficient.  Builds, in FP64 on the GPU,
  * the element metric terms and for every edge the enclosed parallelogram (Sec. 4.2), the
  * projections V^{-1} V_p V_rf^{-1} of both sides (Eq. totalProjection), the least-squares
  * reconstruction (Sec. 4.5) and the edge-normal gradient, folded with D~ = RDG(D1, D2)
  * (Algorithm 2), the edge Jacobian J_f and the upwind convective trace into one
- * Nfp x 2Np flux operator per edge, stored in the chosen precision.
+ * Nfp x 2Np flux operator per edge, stored in the chosen precision.  With RDG_FP32_3XTF32
+ * (N <= 5) no operator is stored: each edge keeps a parameter record (the orthonormal basis
+ * at both sides' apex coordinates, kappa_R, kappa_S, -J_f D~_i, J_f v.n1), and the edge
+ * kernel forms the flux as a tensor-core GEMM against reference matrices of the order (see
+ * rdg_reference_operator which = 6).
  * Errors: RDG_ESTATE (no mesh), RDG_EINVAL, RDG_ERANK, RDG_ENOMEM, RDG_ECUDA. */
 int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision,
                        int interface_rule);
@@ -182,8 +190,13 @@ int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int 
 
 /* Reference operators of order N as the library computed them (host FP64), for checks:
  * which = 0 nodes r,s [2][Np]; 1 Dr [Np][Np]; 2 Ds; 3 LIFT [Np][3 Nfp]; 4 pseudo-inverse of
- * the reconstruction system [Mp][2Np]; 5 mass matrix [Np][Np].  out must hold the
- * stated number of doubles. */
+ * the reconstruction system [Mp][2Np]; 5 mass matrix [Np][Np]; 6 the reference factors of
+ * the GEMM form of the edge operator, X[2 sides][Np m][Nfp i][2 (d_R, d_S)][Np l]: side k's
+ * diffusive edge gradient in rotated node order is
+ * sum_rho kappa_rho sum_m psi_m(alpha_k, beta_k) X[k][m][i][rho][l] (Sec. 4.4-4.5, Eq.
+ * totalProjection: the projection is polynomial in the apex coordinates); 7 the node
+ * permutations [3][Np] (rotated node i of face f is node perm[f][i]); 8 the rotated-order
+ * indices of the shared face's nodes [Nfp].  out must hold the stated number of doubles. */
 int rdg_reference_operator(int N, int which, double* out);
 
 /* Per-edge flux operators in FP64 as built on the GPU: W[n_edges][Nfp][2Np] (host,

@@ -22,7 +22,8 @@ SOURCES = [("refops.cpp", "refops", []), ("api.cpp", "api", []), ("rhs_dispatch.
 for _n in range(1, 7):
     for _t, _tag in (("float", "f"), ("double", "d")):
         SOURCES.append(("rhs_order.cu", "rhs_%s%d" % (_tag, _n),
-                        ["-DRDG_ORDER=%d" % _n, "-DRDG_REAL=%s" % _t, "-DRDG_TAG=%s" % _tag]))
+                        ["-DRDG_ORDER=%d" % _n, "-DRDG_REAL=%s" % _t, "-DRDG_TAG=%s" % _tag,
+                         "-DRDG_TAG_IS_F=%d" % (_tag == "f")]))
 
 
 def nvcc_path():

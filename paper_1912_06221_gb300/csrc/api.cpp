@@ -129,6 +129,16 @@ int64_t w_bytes(int N, int64_t E, int esz) {
   return tiles * w_vecs_per_edge(N, esz) * kTile * 16;
 }
 
+bool uses_gemm(int N, int precision) { return precision == RDG_FP32_3XTF32 && N <= kMaxGemmN; }
+
+// bytes of the per-edge data the edge kernel streams: operators or GEMM-form parameters
+int64_t edge_data_bytes(int N, int64_t E, int precision) {
+  if (uses_gemm(N, precision)) return (E + kTile - 1) / kTile * gemm_param_words(N) * kTile * 16;
+  return w_bytes(N, E, precision == RDG_FP64 ? 8 : 4);
+}
+
+bool valid_precision(int p) { return p == RDG_FP32 || p == RDG_FP64 || p == RDG_FP32_3XTF32; }
+
 const int kFaceA[3] = {0, 1, 2}, kFaceB[3] = {1, 2, 0};
 
 }  // namespace
@@ -384,10 +394,10 @@ int rdg_mesh_counts(const rdg_ctx* ctx, int64_t* nt, int64_t* n_edges, int64_t* 
 int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int precision, int nsrc, int nghost,
                     int64_t* bytes) {
   if (!bytes || N < 1 || N > kMaxN || nt < 0 || n_edges < 0 || n_boundary < 0) return RDG_EINVAL;
-  if (precision != RDG_FP32 && precision != RDG_FP64) return RDG_EINVAL;
+  if (!valid_precision(precision)) return RDG_EINVAL;
   const int64_t esz = precision == RDG_FP64 ? 8 : 4;
   const int64_t Np = np_of(N), Nfp = nfp_of(N);
-  int64_t b = w_bytes(N, n_edges, (int)esz);
+  int64_t b = edge_data_bytes(N, n_edges, precision);
   b += 3 * 4 * n_edges + 3 * 4 * nt;          // k1, k2, face pairs, eref
   b += 3 * nt * Nfp * esz;                     // face fluxes (fused form)
   b += 6 * esz * nt;                           // element coefficients
@@ -400,7 +410,8 @@ int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int 
 
 }  // extern "C"
 
-static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz, double* W_dense) {
+static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz, double* W_dense,
+                          float* P_tiled = nullptr) {
   const int64_t K = ctx->K, E = ctx->E;
   std::vector<int32_t> k1(E), f1(E), k2(E), f2(E);
   std::vector<double> sh(2 * E);
@@ -453,7 +464,7 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
   }
   EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy, ctx->iface,
                  (int64_t)refs.size()};
-  rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, s);
+  rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, P_tiled, s);
   if (rc == RDG_OK && ctx->d_geo && !W_dense)
     rc = setup_elements(K, d_xy, d_D, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
   e = cudaStreamSynchronize(s);
@@ -470,7 +481,8 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   if (!ctx) return RDG_EINVAL;
   if (!ctx->mesh_ok) return fail(ctx, RDG_ESTATE, "rdg_mesh_upload must come first");
   if (N < 1 || N > kMaxN) return fail(ctx, RDG_EINVAL, "order N must be in 1..6");
-  if (precision != RDG_FP32 && precision != RDG_FP64) return fail(ctx, RDG_EINVAL, "precision must be FP32 or FP64");
+  if (!valid_precision(precision))
+    return fail(ctx, RDG_EINVAL, "precision must be RDG_FP32, RDG_FP64 or RDG_FP32_3XTF32");
   if (!D_elem) return fail(ctx, RDG_EINVAL, "D_elem is NULL");
   if (interface_rule != RDG_IFACE_ALG2 && interface_rule != RDG_IFACE_HARMONIC)
     return fail(ctx, RDG_EINVAL, "interface rule must be RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC");
@@ -485,13 +497,14 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   ctx->N = N;
   ctx->prec = precision;
   ctx->esz = precision == RDG_FP64 ? 8 : 4;
+  ctx->gemm = uses_gemm(N, precision);
   ctx->vx = vx;
   ctx->vy = vy;
   ctx->iface = interface_rule;
   ctx->Dk.assign(D_elem, D_elem + ctx->K);
   const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
   const int64_t stb = K * Np * esz;
-  CK(dalloc(&ctx->d_W, w_bytes(N, E, (int)esz), ctx->stream));
+  CK(dalloc(&ctx->d_W, edge_data_bytes(N, E, precision), ctx->stream));
   CK(dalloc(&ctx->d_k1, E * 4, ctx->stream));
   CK(dalloc(&ctx->d_k2, E * 4, ctx->stream));
   CK(dalloc(&ctx->d_eref, 3 * K * 4, ctx->stream));
@@ -514,7 +527,8 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   CK(cudaMemcpyAsync(ctx->d_k2, k2.data(), E * 4, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_eref, ctx->eref.data(), 3 * K * 4, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_u, 0, stb, ctx->stream));
-  int rc = build_edge_ops(ctx, o, ctx->d_W, (int)esz, nullptr);
+  int rc = ctx->gemm ? build_edge_ops(ctx, o, nullptr, (int)esz, nullptr, static_cast<float*>(ctx->d_W))
+                     : build_edge_ops(ctx, o, ctx->d_W, (int)esz, nullptr);
   if (rc != RDG_OK) {
     free_ops(ctx);
     return rc;
@@ -704,7 +718,7 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
     for (auto& e : ev) e = take_event(ctx);
   int rc;
   if (prof) cudaEventRecord(ev[0], st);
-  if constexpr (sizeof(T) == 4) rc = launch_edge_vol32(ctx->N, ea, st);
+  if constexpr (sizeof(T) == 4) rc = ctx->gemm ? launch_gemm32(ctx->N, ea, st) : launch_edge_vol32(ctx->N, ea, st);
   else rc = launch_edge_vol64(ctx->N, ea, st);
   if (prof) {
     cudaEventRecord(ev[1], st);
@@ -873,7 +887,7 @@ int rdg_synchronize(rdg_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (h & kErrBadIndex) return fail(ctx, RDG_ECUDA, "a kernel's index self-check failed (corrupt edge tables)");
-    return fail(ctx, RDG_ETIMEOUT, "a kernel reported an unknown error bit");
+    return fail(ctx, RDG_ETIMEOUT, "a bounded wait for the tensor core gave up (more than 1 s)");
   }
   return RDG_OK;
 }
@@ -894,6 +908,16 @@ int rdg_reference_operator(int N, int which, double* out) {
     case 3: src = &o->LIFT; break;
     case 4: src = &o->Apinv; break;
     case 5: src = &o->M; break;
+    case 6:
+      std::copy(o->X[0].begin(), o->X[0].end(), out);
+      std::copy(o->X[1].begin(), o->X[1].end(), out + o->X[0].size());
+      return RDG_OK;
+    case 7:
+      for (size_t i = 0; i < o->perm.size(); ++i) out[i] = o->perm[i];
+      return RDG_OK;
+    case 8:
+      for (size_t i = 0; i < o->hyp.size(); ++i) out[i] = o->hyp[i];
+      return RDG_OK;
     default: return RDG_EINVAL;
   }
   std::copy(src->begin(), src->end(), out);

@@ -35,7 +35,8 @@ struct rdg_ctx {
   double vx = 0, vy = 0;
   std::vector<double> Dk;
   // device buffers
-  void* d_W = nullptr;
+  bool gemm = false;                // GEMM form of the edge flux (RDG_FP32_3XTF32, N <= kMaxGemmN)
+  void* d_W = nullptr;              // tiled per-edge operators, or the GEMM-form parameter records
   int32_t *d_k1 = nullptr, *d_k2 = nullptr, *d_eref = nullptr;
   void *d_geo = nullptr, *d_flux = nullptr, *d_u = nullptr, *d_u1 = nullptr, *d_u2 = nullptr;
   void *d_S = nullptr, *d_G = nullptr;

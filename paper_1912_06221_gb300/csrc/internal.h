@@ -61,6 +61,7 @@ struct EdgeArgs {
 };
 
 // Device error bits reported through rdg_synchronize.
+constexpr int kErrWaitTimeout = 1;   // a bounded wait for the tensor core gave up
 constexpr int kErrBadIndex = 2;
 
 template <typename T>
@@ -94,6 +95,12 @@ int launch_edge_vol64(int N, const EdgeArgs<double>& a, cudaStream_t s);
 int launch_elem_lite32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s);
 int launch_elem_lite64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s);
 int upload_elem_tables(int device);
+// GEMM form of the edge flux (FP32 state, tcgen05 split 3xTF32), orders 1..kMaxGemmN: the
+// edge kernel reads per-edge parameter records (EdgeArgs::W) and also computes the volume
+// terms; the element kernel is the same as the stored-operator form's.
+constexpr int kMaxGemmN = 5;
+int launch_gemm32(int N, const EdgeArgs<float>& a, cudaStream_t s);
+int gemm_param_words(int N);   // 16-byte words of an edge's parameter record
 
 // ---- setup (FP64) -------------------------------------------------------------------
 struct EdgeSetupIn {
@@ -111,7 +118,10 @@ struct EdgeSetupIn {
   int64_t nrefs;           // doubles in refs (checked against the order's layout)
 };
 
-int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s);
+// Per edge: the tiled operator W (W_tiled, elem_bytes per value), the dense FP64 operator
+// (W_dense), and/or the GEMM-form parameter record (P_tiled, FP32); any may be null.
+int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, float* P_tiled,
+                cudaStream_t s);
 int setup_elements(int64_t K, const double* xy, const double* D, double vx, double vy, void* geo, int elem_bytes,
                    cudaStream_t s);
 // Reference constants for the setup kernel, flattened in the order setup.cu reads them.

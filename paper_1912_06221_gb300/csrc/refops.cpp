@@ -359,6 +359,49 @@ std::unique_ptr<RefOps> build(int N, const char** err) {
         for (int m = 0; m < Np; ++m) o->dvec[k][i] += PA[(size_t)i * 2 * Np + k * Np + m] * chat[m];
     }
   }
+  // GEMM form: C_m[n][j] = int_T psi_j(A_n(alpha, beta)) psi_m(alpha, beta), exact with a
+  // collapsed Gauss rule (the integrand has degree <= 2N), A_n the affine image of node n.
+  {
+    std::vector<double> qx, qw;
+    gauss_legendre(N + 3, qx, qw);
+    Mat C((size_t)Np * Np * Np, 0.0);   // [m][n][j]
+    std::vector<double> pm(Np), pj(Np);
+    for (size_t qa = 0; qa < qx.size(); ++qa)
+      for (size_t qb = 0; qb < qx.size(); ++qb) {
+        const double a = qx[qa], b = qx[qb];
+        const double al = (1 + a) * (1 - b) / 2 - 1, be = b, w = qw[qa] * qw[qb] * (1 - b) / 2;
+        simplex_basis(N, al, be, pm.data(), nullptr, nullptr);
+        for (int n = 0; n < Np; ++n) {
+          const double rn = o->r[n], sn = o->s[n];
+          const double Ar = -(rn + sn) / 2 * al + (rn + 1) / 2 - (sn + 1) / 2;
+          const double As = -(rn + sn) / 2 * be - (rn + 1) / 2 + (sn + 1) / 2;
+          simplex_basis(N, Ar, As, pj.data(), nullptr, nullptr);
+          for (int m = 0; m < Np; ++m)
+            for (int j = 0; j < Np; ++j) C[((size_t)m * Np + n) * Np + j] += w * pm[m] * pj[j];
+        }
+      }
+    for (int k = 0; k < 2; ++k) {
+      o->X[k].assign((size_t)Np * Nfp * 2 * Np, 0.0);
+      for (int m = 0; m < Np; ++m) {
+        Mat Cm(C.begin() + (size_t)m * Np * Np, C.begin() + (size_t)(m + 1) * Np * Np);
+        Mat CV = matmul(Cm, o->Vinv, Np, Np, Np);
+        Mat XR = matmul(o->QRV[k], CV, Nfp, Np, Np), XS = matmul(o->QSV[k], CV, Nfp, Np, Np);
+        for (int i = 0; i < Nfp; ++i)
+          for (int l = 0; l < Np; ++l) {
+            o->X[k][(((size_t)m * Nfp + i) * 2 + 0) * Np + l] = XR[(size_t)i * Np + l];
+            o->X[k][(((size_t)m * Nfp + i) * 2 + 1) * Np + l] = XS[(size_t)i * Np + l];
+          }
+      }
+    }
+    // the shared face in rotated order: the same nodes for every face f
+    o->hyp.assign(Nfp, -1);
+    for (int f = 0; f < 3; ++f)
+      for (int q = 0; q < Nfp; ++q) {
+        const int l = o->perm[f * Np + o->Fmask[f * Nfp + q]];
+        if (f == 0) o->hyp[q] = l;
+        else if (o->hyp[q] != l) { *err = "rotated face nodes differ between faces"; return nullptr; }
+      }
+  }
   return o;
 }
 

@@ -34,6 +34,15 @@ struct RefOps {
   // Algorithm 2 for element-constant D: D~(diagonal node i) = D1 dvec[0][i] + D2 dvec[1][i],
   // the reconstruction of the two constants through the same least-squares operator
   std::vector<double> dvec[2];
+  // Reference factors of the on-the-fly flux (the GEMM form of the edge operator).  The
+  // projection V_p(alpha, beta) of side k is a polynomial of degree <= N in the apex
+  // coordinates (the map A is affine in them), expanded in the orthonormal basis:
+  // V_p = sum_m psi_m(alpha, beta) C_m.  Then the side's diffusive operator in the rotated
+  // node order is  sum_rho kappa_rho sum_m psi_m(alpha, beta) X[k][m][i][rho][l]  with
+  // X[k][m][.][rho][.] = Q^rho_k C_m Vinv (Q^R = QRV, Q^S = QSV), layout
+  // [m][Nfp][2][Np] per side.
+  std::vector<double> X[2];
+  std::vector<int> hyp;              // [Nfp] rotated-order indices of the shared face's nodes
 };
 
 // Builds (and caches) the operators of order N; returns nullptr if N is out of range or the

@@ -39,6 +39,25 @@ int launch_edge_vol64(int N, const EdgeArgs<double>& a, cudaStream_t s) { RDG_SW
 int launch_elem_lite32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s) { RDG_SWITCH(f, CALL_ELEM_LITE) }
 int launch_elem_lite64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_ELEM_LITE) }
 
+int launch_gemm_f1(const EdgeArgs<float>& a, cudaStream_t s);
+int launch_gemm_f2(const EdgeArgs<float>& a, cudaStream_t s);
+int launch_gemm_f3(const EdgeArgs<float>& a, cudaStream_t s);
+int launch_gemm_f4(const EdgeArgs<float>& a, cudaStream_t s);
+int launch_gemm_f5(const EdgeArgs<float>& a, cudaStream_t s);
+
+int launch_gemm32(int N, const EdgeArgs<float>& a, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_gemm_f1(a, s);
+    case 2: return launch_gemm_f2(a, s);
+    case 3: return launch_gemm_f3(a, s);
+    case 4: return launch_gemm_f4(a, s);
+    case 5: return launch_gemm_f5(a, s);
+  }
+  return RDG_EINVAL;
+}
+
+int gemm_param_words(int N) { return (2 * np_of(N) + nfp_of(N) + 3 + 3) / 4; }
+
 int upload_elem_tables(int device) {
   (void)device;
   int (*fns[])() = {upload_tab_f1, upload_tab_f2, upload_tab_f3, upload_tab_f4, upload_tab_f5, upload_tab_f6,

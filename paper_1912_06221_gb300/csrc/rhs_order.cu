@@ -24,13 +24,46 @@ __constant__ RDG_REAL c_tab[kTabN];
 #define RDG_TAB c_tab
 #include "rhs_kernels.cuh"
 
+// FP32 objects of orders 1..kMaxGemmN also hold the GEMM form of the edge flux.
+#define RDG_GEMM (RDG_TAG_IS_F && RDG_ORDER <= 5)
+#if RDG_GEMM
+#include <cstring>
+
+#include "gemm_kernels.cuh"
+namespace {
+using GS = rdg::gemm::Shape<kN>;
+__device__ __align__(16) float4 g_xb[4 * GS::BTILE / 16];
+__device__ int g_gtab[3 * kNp + kN + 1];
+}  // namespace
+#endif
+
 namespace rdg {
 
 int RDG_CAT(upload_tab_, RDG_CAT(RDG_TAG, RDG_ORDER))() {
   std::vector<RDG_REAL> t = pack_elem_table<RDG_REAL>(kN);
   if ((int)t.size() != kTabN) return RDG_EINVAL;
-  return cudaMemcpyToSymbol(c_tab, t.data(), t.size() * sizeof(RDG_REAL)) == cudaSuccess ? RDG_OK : RDG_ECUDA;
+  if (cudaMemcpyToSymbol(c_tab, t.data(), t.size() * sizeof(RDG_REAL)) != cudaSuccess) return RDG_ECUDA;
+#if RDG_GEMM
+  const RefOps* o = get_refops(kN, nullptr);
+  if (!o) return RDG_EINVAL;
+  std::vector<float> xb = gemm::pack_gemm_operand<kN>(*o);
+  std::vector<int> gt = gemm::pack_gemm_table<kN>(*o);
+  if (xb.size() * 4 != sizeof(g_xb) || gt.size() * 4 != sizeof(g_gtab)) return RDG_EINVAL;
+  if (cudaMemcpyToSymbol(g_xb, xb.data(), sizeof(g_xb)) != cudaSuccess) return RDG_ECUDA;
+  if (cudaMemcpyToSymbol(g_gtab, gt.data(), sizeof(g_gtab)) != cudaSuccess) return RDG_ECUDA;
+#endif
+  return RDG_OK;
 }
+
+#if RDG_GEMM
+int RDG_CAT(launch_gemm_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<float>& a, cudaStream_t s) {
+  void* xb = nullptr;
+  void* gt = nullptr;
+  if (cudaGetSymbolAddress(&xb, g_xb) != cudaSuccess || cudaGetSymbolAddress(&gt, g_gtab) != cudaSuccess)
+    return RDG_ECUDA;
+  return gemm::launch_gemm_t<kN>(a, static_cast<const float4*>(xb), static_cast<const int*>(gt), s);
+}
+#endif
 
 int RDG_CAT(launch_edge_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_REAL>& a, cudaStream_t s) {
   return launch_edge_t<RDG_REAL, kN>(a, s);

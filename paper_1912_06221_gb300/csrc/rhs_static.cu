@@ -38,6 +38,8 @@ extern "C" int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_de
   if ((((uintptr_t)u_dev) & 15u) || (((uintptr_t)rhs_dev) & 15u))
     return fail_static(ctx, RDG_EINVAL, "device arrays must be 16-byte aligned");
   if (u_dev == rhs_dev) return fail_static(ctx, RDG_EINVAL, "u and rhs must not overlap");
+  if (ctx->gemm)
+    return fail_static(ctx, RDG_ESTATE, "rdg_rhs_eval_static needs the stored operators (not RDG_FP32_3XTF32)");
   const size_t need = (size_t)ctx->E * nfp_of(ctx->N) * ctx->esz;
   if (need > kStaticFluxBytes)
     return fail_static(ctx, RDG_EINVAL,

@@ -170,7 +170,7 @@ __host__ __device__ constexpr int setup_ref_count() {
 // over all 32 lanes.
 template <int N>
 __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeSetupIn in, void* Wt, int elem_bytes,
-                                                                            double* Wd) {
+                                                                            double* Wd, float* Pt) {
   constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP, WARPS = setup_warps<N>();
   constexpr int RT = setup_ref_count<N>();
   __shared__ double sR[RT];
@@ -227,6 +227,30 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   const int VW = 16 / elem_bytes;
   const int QW = (NW + VW - 1) / VW;
 
+  if (Pt) {
+    // GEMM-form parameter record (FP32): psi_m(alpha_k, beta_k) of both sides, kappa_R,
+    // kappa_S, -J_f D~_i and J_f (v.n1), tiled [edge/32][16-byte word][lane]
+    constexpr int PW = 2 * NP + NFP + 3, PW4 = (PW + 3) / 4;
+    auto put = [&](int j, double x) {
+      Pt[(((tile * PW4 + j / 4) * kTile) + le) * 4 + (j % 4)] = (float)x;
+    };
+    if (lane < 2) {
+      double ph[NP];
+      simplex_basis_tab<N>(al[lane], be[lane], jac, ph);
+      for (int m = 0; m < NP; ++m) put(lane * NP + m, ph[m]);
+    } else if (lane == 2) {
+      put(2 * NP, kR);
+      put(2 * NP + 1, kS);
+      for (int i = 0; i < NFP; ++i) {
+        const double Dt = in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
+                                                         : D1v * dvec[i] + D2v * dvec[NFP + i];
+        put(2 * NP + 2 + i, -Jf * Dt);
+      }
+      put(2 * NP + 2 + NFP, Jf * vn);
+      for (int j = PW; j < 4 * PW4; ++j) put(j, 0.0);
+    }
+    if (!Wt && !Wd) return;
+  }
   for (int side = 0; side < 2; ++side) {
     if (lane < NP) {
       const double rn = rr[lane], sn = ss[lane];
@@ -303,23 +327,25 @@ __global__ void set_time_kernel(TimeState* ts, double t0) {
 }  // namespace
 
 template <int N>
-int launch_setup(const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s) {
+int launch_setup(const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, float* P_tiled,
+                 cudaStream_t s) {
   constexpr int W = setup_warps<N>();
   if (in.nrefs != setup_ref_count<N>()) return RDG_EINVAL;
   const unsigned grid = (unsigned)((in.E + W - 1) / W);
-  edge_setup_kernel<N><<<grid, 32 * W, 0, s>>>(in, W_tiled, elem_bytes, W_dense);
+  edge_setup_kernel<N><<<grid, 32 * W, 0, s>>>(in, W_tiled, elem_bytes, W_dense, P_tiled);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
 
-int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, cudaStream_t s) {
+int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, float* P_tiled,
+                cudaStream_t s) {
   if (in.E == 0) return RDG_OK;
   switch (N) {
-    case 1: return launch_setup<1>(in, W_tiled, elem_bytes, W_dense, s);
-    case 2: return launch_setup<2>(in, W_tiled, elem_bytes, W_dense, s);
-    case 3: return launch_setup<3>(in, W_tiled, elem_bytes, W_dense, s);
-    case 4: return launch_setup<4>(in, W_tiled, elem_bytes, W_dense, s);
-    case 5: return launch_setup<5>(in, W_tiled, elem_bytes, W_dense, s);
-    case 6: return launch_setup<6>(in, W_tiled, elem_bytes, W_dense, s);
+    case 1: return launch_setup<1>(in, W_tiled, elem_bytes, W_dense, P_tiled, s);
+    case 2: return launch_setup<2>(in, W_tiled, elem_bytes, W_dense, P_tiled, s);
+    case 3: return launch_setup<3>(in, W_tiled, elem_bytes, W_dense, P_tiled, s);
+    case 4: return launch_setup<4>(in, W_tiled, elem_bytes, W_dense, P_tiled, s);
+    case 5: return launch_setup<5>(in, W_tiled, elem_bytes, W_dense, P_tiled, s);
+    case 6: return launch_setup<6>(in, W_tiled, elem_bytes, W_dense, P_tiled, s);
     default: return RDG_EINVAL;
   }
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "librdg.so")
 
 RDG_OK, RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA, RDG_EMESH, RDG_ERANK, RDG_ETIMEOUT, RDG_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 BC_PERIODIC, BC_DIRICHLET = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_3XTF32 = 0, 1, 2
 TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
 IFACE_ALG2, IFACE_HARMONIC = 0, 1
 ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
@@ -109,7 +109,8 @@ def query_bytes(N, nt, n_edges, n_boundary, precision, nsrc=0, nghost=0):
 
 def reference_operator(N, which):
     Np, Nfp, Mp = np_of(N), N + 1, (N + 1) ** 2
-    shape = {0: (2, Np), 1: (Np, Np), 2: (Np, Np), 3: (Np, 3 * Nfp), 4: (Mp, 2 * Np), 5: (Np, Np)}[which]
+    shape = {0: (2, Np), 1: (Np, Np), 2: (Np, Np), 3: (Np, 3 * Nfp), 4: (Mp, 2 * Np), 5: (Np, Np),
+             6: (2, Np, Nfp, 2, Np), 7: (3, Np), 8: (Nfp,)}[which]
     out = np.zeros(shape)
     _check(load().rdg_reference_operator(N, which, _ptr(out)))
     return out
@@ -126,7 +127,7 @@ class Solver:
         self.device = device
         self.N, self.Np, self.Nfp = N, np_of(N), N + 1
         self.precision = precision
-        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.dtype = torch.float64 if precision == FP64 else torch.float32   # FP32 and FP32_3XTF32
         self.np_dtype = np.float64 if precision == FP64 else np.float32
         self.stream, handle = _stream_handle(torch, stream, device)
         ctx = _P()
