@@ -148,6 +148,38 @@ class EdgeOps:
         ops = self.mesh.ops
         return c @ ops.phi(ops.diag_R, ops.diag_S).T
 
+    def flux_algorithm1(self, c, D1, D2):
+        """Algorithm 1 (Sec. 3, Eq. NDG_diffusion_once_matrixForm_reference_general) for
+        element-constant D: n1 . RDG(D_p^1 grad u~^1, D_p^2 grad u~^2) at the diagonal nodes.
+
+        The steps in the paper's order, for reconstruction coefficients c [E, Mp] of u~:
+        Separation - u~ L2-projected onto P_N on each sub-triangle Omega'_k, in side k's frame
+        (side 1: (r,s) = (R,S); side 2: (r,s) = (-R,-S)): modal coefficients A_k c.
+        D_p^k = V_pk D^k - the projection of an element-constant D is that constant.
+        Grad - nodal gradient of u~^k on Omega'_k in physical coordinates, d/dR = +-d/dr.
+        Product - D_p^k grad u~^k at the sub-triangle nodes.
+        RDG - least-squares reconstruction of each component from the two sub-triangles'
+        modal data, evaluated at the diagonal nodes; then n1 . (.)."""
+        ops = self.mesh.ops
+        Rx, Ry, Sx, Sy = self.Rx.T
+        Phi = ops.phi(ops.diag_R, ops.diag_S)
+        out = np.zeros((c.shape[0], ops.Nfp))
+        for comp in range(2):
+            dRphys = Rx if comp == 0 else Ry     # d/dx = R_x d/dR + S_x d/dS (y likewise)
+            dSphys = Sx if comp == 0 else Sy
+            modal = []
+            for side, (Ak, sgn, Dk) in enumerate(((ops.A1, 1.0, D1), (ops.A2, -1.0, D2))):
+                uk = c @ Ak.T                       # Separation: modal on Omega'_k [E, Np]
+                nod = uk @ ops.V.T                  # nodal values at the sub-triangle nodes
+                dr = nod @ ops.Dr.T
+                ds = nod @ ops.Ds.T
+                g = sgn * (dRphys[:, None] * dr + dSphys[:, None] * ds)
+                w = np.asarray(Dk)[:, None] * g     # Product with D_p^k
+                modal.append(w @ ops.Vinv.T)        # modal data of the component on Omega'_k
+            cc = np.concatenate(modal, axis=1) @ ops.Apinv.T   # RDG of the component
+            out += self.n1[:, comp:comp + 1] * (cc @ Phi.T)
+        return out
+
     def reconstruct_D(self, D1, D2):
         """Algorithm 2: D~ = RDG(D1, D2) for element-constant D, values at diagonal nodes."""
         Np = self.mesh.ops.Np

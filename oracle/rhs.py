@@ -34,6 +34,9 @@ class Problem:
     source and Dirichlet ghost data (lists of (nodal profile, kind, omega)).
 
     interface: how the edge diffusion coefficient D~ is formed for element-wise D.
+      "alg1"      the paper's Algorithm 1: the edge flux is n . RDG(D_p^1 grad u~^1,
+                  D_p^2 grad u~^2) with Separation read as the L2 projection of u~ onto
+                  each sub-triangle (EdgeOps.flux_algorithm1);
       "alg2"      the paper's Algorithm 2, D~ = RDG(D1, D2) on the diagonal;
       "harmonic"  2 D1 D2 / (D1 + D2), not in the paper: a stabilised variant for
                   high-contrast jumps (with "alg2" such jumps give operator eigenvalues with
@@ -54,7 +57,11 @@ class Problem:
         self.f2 = np.array([e[3] for e in m.edges])
         self.interior = self.k2 >= 0
         D2 = np.where(self.interior, self.D[np.maximum(self.k2, 0)], self.D[self.k1])
-        if interface == "alg2":
+        self.interface = interface
+        self.D1e, self.D2e = self.D[self.k1], D2
+        if interface == "alg1":
+            self.Dt = None
+        elif interface == "alg2":
             self.Dt = self.eops.reconstruct_D(self.D[self.k1], D2)
         elif interface == "harmonic":
             D1 = self.D[self.k1]
@@ -81,14 +88,17 @@ class Problem:
         if self.bnd.size:
             u2[self.bnd] = self.ghost_values(t)
         c = self.eops.reconstruct(u1, u2)
-        g = self.eops.edge_normal_gradient(c)
+        if self.interface == "alg1":
+            Dg = self.eops.flux_algorithm1(c, self.D1e, self.D2e)
+        else:
+            Dg = self.Dt * self.eops.edge_normal_gradient(c)
         # upwind convective trace
         vn = self.eops.n1 @ self.v
         tr1 = np.take_along_axis(u1, np.stack([ops.Fmask[f] for f in self.f1]), axis=1)
         f2i = np.where(self.interior, self.f2, 1)
         tr2 = np.take_along_axis(u2, np.stack([ops.Fmask[f][::-1] for f in f2i]), axis=1)
         up = np.where((vn >= 0)[:, None], tr1, tr2)
-        return vn[:, None] * up - self.Dt * g
+        return vn[:, None] * up - Dg
 
     def rhs(self, u, t=0.0):
         m = self.mesh

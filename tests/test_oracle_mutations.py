@@ -118,3 +118,27 @@ def test_mutation_dropped_volume_term(monkeypatch):
         return out
     monkeypatch.setattr(orhs.Problem, "rhs", bad)
     _fails(TR.test_rhs_exact_for_global_polynomials, 2)
+
+
+def test_mutation_alg1_side2_gradient_not_reflected(monkeypatch):
+    """Algorithm 1 with side 2's gradient taken as if its frame were side 1's (no sign flip
+    of d/dR, d/dS under the point reflection)."""
+    from tests import test_oracle_alg1 as T1
+
+    def bad(self, c, D1, D2):
+        ops = self.mesh.ops
+        Rx, Ry, Sx, Sy = self.Rx.T
+        Phi = ops.phi(ops.diag_R, ops.diag_S)
+        out = np.zeros((c.shape[0], ops.Nfp))
+        for comp in range(2):
+            dRp = Rx if comp == 0 else Ry
+            dSp = Sx if comp == 0 else Sy
+            modal = []
+            for Ak, Dk in ((ops.A1, D1), (ops.A2, D2)):
+                nod = (c @ Ak.T) @ ops.V.T
+                g = dRp[:, None] * (nod @ ops.Dr.T) + dSp[:, None] * (nod @ ops.Ds.T)
+                modal.append((np.asarray(Dk)[:, None] * g) @ ops.Vinv.T)
+            out += self.n1[:, comp:comp + 1] * ((np.concatenate(modal, axis=1) @ ops.Apinv.T) @ Phi.T)
+        return out
+    monkeypatch.setattr(ardg.EdgeOps, "flux_algorithm1", bad)
+    _fails(T1.test_alg1_exact_for_global_polynomials, 2)

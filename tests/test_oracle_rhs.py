@@ -156,11 +156,15 @@ def _jump_problem(N, interface, m=6):
 def test_high_contrast_jump_stability(N):
     """Element-wise D with a 1e4 jump across a circle (the circle-pulse recipe on a 6x6x2
     mesh): with the paper's Algorithm 2 (D~ = mean on the edge) the operator has an
-    eigenvalue with a clearly positive real part; the harmonic interface coefficient gives a
-    stable operator."""
+    eigenvalue with a clearly positive real part; Algorithm 1 and the harmonic interface
+    coefficient give stable operators."""
     lam = np.linalg.eigvals(_jump_problem(N, "alg2").dense_operator())
     assert lam.real.max() > 1e-2 * np.abs(lam).max()
     lam = np.linalg.eigvals(_jump_problem(N, "harmonic").dense_operator())
+    assert lam.real.max() < 1e-10 * np.abs(lam).max()
+    # the paper's Algorithm 1 (D weighted inside each sub-triangle before the second
+    # reconstruction) is stable too
+    lam = np.linalg.eigvals(_jump_problem(N, "alg1").dense_operator())
     assert lam.real.max() < 1e-10 * np.abs(lam).max()
 
 
