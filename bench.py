@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--rk-steps", type=int, default=RK_STEPS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32"],
+                   help="fp32: stored per-edge operators; tf32: GEMM form on the tensor cores (split 3xTF32)")
     p.add_argument("--serve", action="store_true", help="run the request-stream server instead")
     p.add_argument("--serve-requests", type=int, default=200)
     p.add_argument("--serve-slots", type=int, default=32)
@@ -214,7 +216,8 @@ def workload_config(args):
                         "D=1 in r<0.25 else 1e-4, Gaussian w=0.05, %d SSP-RK3 steps at 0.5x stability bound"
                         % (args.m, args.m, 2 * args.m * args.m, args.rk_steps),
             "N": N_ORDER, "triangles": 2 * args.m * args.m, "rk_steps_per_bench_step": args.rk_steps,
-            "rhs_per_bench_step": 3 * args.rk_steps, "precision": "fp32",
+            "rhs_per_bench_step": 3 * args.rk_steps,
+            "precision": "fp32" if args.precision == "fp32" else "fp32 state, edge flux as split-3xTF32 tensor-core GEMM",
             "l2_flush": "256 MB buffer written between timed steps (outside the events)",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -252,7 +255,9 @@ def run_ours(args):
     rdg.load()
     from synth import circle_pulse
     w = circle_pulse(m=args.m, N=N_ORDER)
-    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32, device=local)
+    gemm = args.precision == "tf32"
+    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32_3XTF32 if gemm else rdg.FP32,
+                   device=local)
     stream = torch.cuda.current_stream()
     xyn = s.node_coords()
     u0_host = w.u0(xyn[..., 0], xyn[..., 1]).astype(np.float32)
@@ -301,6 +306,8 @@ def run_ours(args):
     # fused edge kernel: operator stream, edge ids, flux write, stage input (read once),
     # volume-term write, five element coefficients
     edge_bytes = E * (Nfp * 2 * Np * 4 + 8 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
+    if gemm:   # parameter records (16-byte words) instead of operators, plus the face-pair word
+        edge_bytes = E * (((2 * Np + Nfp + 3 + 3) // 4) * 16 + 12 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
     # surface/stage kernel, averaged over the three stages (the step start is read in two):
     # volume term, stage input, step start, output, edge ids, 1/J, face fluxes
     elem_bytes = int(K * ((3 + 2.0 / 3.0) * Np * 4 + 12 + 4) + E * Nfp * 4)
@@ -308,8 +315,9 @@ def run_ours(args):
     edge_avg = edge_ms / edge_n
     elem_avg = elem_ms / elem_n
     ach = edge_bytes / (edge_avg / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "edge_flux_kernel<float,4,VOL=1>", "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "peak_source": peak_kind, "traffic": profiled_traffic(args),
+    roof = {"bound": "hbm", "kernel": "edge_gemm_kernel<4>" if gemm else "edge_flux_kernel<float,4,VOL=1>",
+            "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": peak_kind, "traffic": None if gemm else profiled_traffic(args),
             "traffic_source": "profiles/stage_kernels_circle_pulse_N4_m256_fp32.md (ncu, one launch)",
             "alg_bytes_per_launch": edge_bytes, "avg_launch_us": edge_avg * 1e3,
             "share_of_kernel_time": edge_ms / (edge_ms + elem_ms),
@@ -335,7 +343,9 @@ def run_ours(args):
         # the same solve in FP64, for the paper's interface rule (Algorithm 2) and the
         # harmonic one: FP32-vs-FP64 differences at t_final and the size of the solution
         fp64 = {}
-        for rule, name in ((rdg.IFACE_ALG2, "algorithm2"), (rdg.IFACE_HARMONIC, "harmonic")):
+        u64s = {}
+        for rule, name in ((rdg.IFACE_ALG2, "algorithm2"), (rdg.IFACE_HARMONIC, "harmonic"),
+                           (rdg.IFACE_ALG1, "algorithm1")):
             if rule == rdg.IFACE_ALG2:
                 u32 = u_fp32
             else:
@@ -357,11 +367,42 @@ def run_ours(args):
             torch.cuda.synchronize()
             t64 = a.elapsed_time(b)
             u64 = s64.get_state_host()
+            u64s[name] = u64
             fp64[name] = {"fp64_value": s.K * s.Np * 3 * nrk / (t64 / 1e3) / 1e9, "unit": UNIT,
                           "fp32_rel_l2_vs_fp64": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
                           "fp32_rel_linf_vs_fp64": float(np.abs(u32 - u64).max() / np.abs(u64).max()),
                           "max_abs_u_t_final": float(np.abs(u64).max()), "t_final": nrk * dt}
             s64.close()
+
+    # the same solve with the GEMM form of the edge flux (tcgen05, split 3xTF32)
+    tf32 = None
+    if fp64 and not gemm:
+        # harmonic interface rule: the same kernels and speed as Algorithm 2, but a stable
+        # operator, so the difference to FP64 is rounding and not amplified growth
+        st = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32_3XTF32, device=local,
+                        interface=rdg.IFACE_HARMONIC)
+        st.set_state(u0)
+        st.solve_to_time(0.0, dt, nrk)
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(max(2, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.set_state(u0)
+            st.solve_to_time(0.0, dt, nrk)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b))
+        ut = st.get_state_host().astype(np.float64)
+        st.synchronize()
+        st.close()
+        u64 = u64s["harmonic"]
+        tf32 = {"value": s.K * s.Np * 3 * nrk / (float(np.median(tt)) / 1e3) / 1e9, "unit": UNIT,
+                "kernel": "edge_gemm_kernel<4> (tcgen05.mma kind::tf32, split 3xTF32) + elem_lite_kernel",
+                "rel_l2_vs_fp64": float(np.linalg.norm(ut - u64) / np.linalg.norm(u64)),
+                "rel_linf_vs_fp64": float(np.abs(ut - u64).max() / np.abs(u64).max()),
+                "interface": "harmonic"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,7 +418,7 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
                     "d2h_bytes_per_step": int(out_host.nbytes)},
             "gpu_launches": per_solve * args.steps,
-            "fp64_gpu": fp64}
+            "fp64_gpu": fp64, "fp32_3xtf32": tf32}
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()

@@ -59,13 +59,16 @@ enum { RDG_BC_PERIODIC = 0, RDG_BC_DIRICHLET = 1 };
 /* Precision of the state and the hot path.  RDG_FP32_3XTF32: FP32 state with the edge flux in
  * its GEMM form on the tensor cores (split 3xTF32 products against shared reference
  * matrices, per-edge parameters instead of stored operators, see rdg_operator_setup); orders
- * N = 1..5 (N = 6 runs the RDG_FP32 path). */
+ * N = 1..5 with RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC (otherwise the RDG_FP32 path runs). */
 enum { RDG_FP64 = 0, RDG_FP32 = 1, RDG_FP32_3XTF32 = 2 };
 enum { RDG_TAU_CONST = 0, RDG_TAU_COS = 1, RDG_TAU_SIN = 2 };
-/* Edge diffusion coefficient for element-wise D: the paper's Algorithm 2 (D~ = RDG(D1, D2)
- * on the diagonal) or the harmonic mean 2 D1 D2 / (D1 + D2) (not in the paper: stable for
- * high-contrast jumps, where Algorithm 2 gives growing modes). Equal when D1 = D2. */
-enum { RDG_IFACE_ALG2 = 0, RDG_IFACE_HARMONIC = 1 };
+/* Edge diffusion for element-wise D: the paper's Algorithm 2 (D~ = RDG(D1, D2) on the
+ * diagonal times n . grad u~), the harmonic mean 2 D1 D2 / (D1 + D2) times n . grad u~ (not
+ * in the paper: stable for high-contrast jumps, where Algorithm 2 gives growing modes), or
+ * the paper's Algorithm 1 (n . RDG(D1 grad u~^1, D2 grad u~^2), u~^k the L2 projection of u~
+ * onto sub-triangle k; also stable for such jumps).  Algorithm 2 and the harmonic rule agree
+ * when D1 = D2; Algorithm 1 agrees with them on linear data. */
+enum { RDG_IFACE_ALG2 = 0, RDG_IFACE_HARMONIC = 1, RDG_IFACE_ALG1 = 2 };
 #define RDG_MAX_FORCING_TERMS 4
 
 /* Library version string. */

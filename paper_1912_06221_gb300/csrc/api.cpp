@@ -129,7 +129,9 @@ int64_t w_bytes(int N, int64_t E, int esz) {
   return tiles * w_vecs_per_edge(N, esz) * kTile * 16;
 }
 
-bool uses_gemm(int N, int precision) { return precision == RDG_FP32_3XTF32 && N <= kMaxGemmN; }
+bool uses_gemm(int N, int precision, int iface = RDG_IFACE_ALG2) {
+  return precision == RDG_FP32_3XTF32 && N <= kMaxGemmN && iface != RDG_IFACE_ALG1;
+}
 
 // bytes of the per-edge data the edge kernel streams: operators or GEMM-form parameters
 int64_t edge_data_bytes(int N, int64_t E, int precision) {
@@ -397,7 +399,9 @@ int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int 
   if (!valid_precision(precision)) return RDG_EINVAL;
   const int64_t esz = precision == RDG_FP64 ? 8 : 4;
   const int64_t Np = np_of(N), Nfp = nfp_of(N);
-  int64_t b = edge_data_bytes(N, n_edges, precision);
+  // the stored operators: an upper bound for every mode (the GEMM form's parameter records
+  // are smaller, and it falls back to stored operators for N = 6 and Algorithm 1)
+  int64_t b = w_bytes(N, n_edges, (int)esz);
   b += 3 * 4 * n_edges + 3 * 4 * nt;          // k1, k2, face pairs, eref
   b += 3 * nt * Nfp * esz;                     // face fluxes (fused form)
   b += 6 * esz * nt;                           // element coefficients
@@ -484,8 +488,8 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   if (!valid_precision(precision))
     return fail(ctx, RDG_EINVAL, "precision must be RDG_FP32, RDG_FP64 or RDG_FP32_3XTF32");
   if (!D_elem) return fail(ctx, RDG_EINVAL, "D_elem is NULL");
-  if (interface_rule != RDG_IFACE_ALG2 && interface_rule != RDG_IFACE_HARMONIC)
-    return fail(ctx, RDG_EINVAL, "interface rule must be RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC");
+  if (interface_rule != RDG_IFACE_ALG2 && interface_rule != RDG_IFACE_HARMONIC && interface_rule != RDG_IFACE_ALG1)
+    return fail(ctx, RDG_EINVAL, "interface rule must be RDG_IFACE_ALG2, RDG_IFACE_HARMONIC or RDG_IFACE_ALG1");
   if (!std::isfinite(vx) || !std::isfinite(vy)) return fail(ctx, RDG_EINVAL, "velocity not finite");
   for (int64_t k = 0; k < ctx->K; ++k)
     if (!(D_elem[k] > 0) || !std::isfinite(D_elem[k])) return fail(ctx, RDG_EINVAL, "D must be positive and finite");
@@ -497,14 +501,14 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   ctx->N = N;
   ctx->prec = precision;
   ctx->esz = precision == RDG_FP64 ? 8 : 4;
-  ctx->gemm = uses_gemm(N, precision);
+  ctx->gemm = uses_gemm(N, precision, interface_rule);
   ctx->vx = vx;
   ctx->vy = vy;
   ctx->iface = interface_rule;
   ctx->Dk.assign(D_elem, D_elem + ctx->K);
   const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
   const int64_t stb = K * Np * esz;
-  CK(dalloc(&ctx->d_W, edge_data_bytes(N, E, precision), ctx->stream));
+  CK(dalloc(&ctx->d_W, ctx->gemm ? edge_data_bytes(N, E, precision) : w_bytes(N, E, (int)esz), ctx->stream));
   CK(dalloc(&ctx->d_k1, E * 4, ctx->stream));
   CK(dalloc(&ctx->d_k2, E * 4, ctx->stream));
   CK(dalloc(&ctx->d_eref, 3 * K * 4, ctx->stream));

@@ -344,6 +344,36 @@ std::unique_ptr<RefOps> build(int N, const char** err) {
     o->QRV[k] = matmul(qr, o->Vinv, Nfp, Np, Np);
     o->QSV[k] = matmul(qs, o->Vinv, Nfp, Np, Np);
   }
+  // Algorithm 1 factors: Y^rho_j = s_j Phi_diag A+_j (Vinv D_rho V) A_j, then Y A+_k Vinv
+  {
+    Mat Phi((size_t)Nfp * Mp);
+    for (int i = 0; i < Nfp; ++i)
+      for (int ia = 0; ia <= N; ++ia)
+        for (int ib = 0; ib <= N; ++ib) Phi[(size_t)i * Mp + ia * (N + 1) + ib] = legn(ia, -t[i]) * legn(ib, t[i]);
+    Mat DrM = matmul(matmul(o->Vinv, o->Dr, Np, Np, Np), o->V, Np, Np, Np);
+    Mat DsM = matmul(matmul(o->Vinv, o->Ds, Np, Np, Np), o->V, Np, Np, Np);
+    Mat Ap[2], Ak[2];
+    for (int k = 0; k < 2; ++k) {
+      Ap[k].resize((size_t)Mp * Np);
+      Ak[k].resize((size_t)Np * Mp);
+      for (int a = 0; a < Mp; ++a)
+        for (int j = 0; j < Np; ++j) Ap[k][(size_t)a * Np + j] = o->Apinv[(size_t)a * 2 * Np + k * Np + j];
+      for (int j = 0; j < Np; ++j)
+        for (int a = 0; a < Mp; ++a) Ak[k][(size_t)j * Mp + a] = A[(size_t)(k * Np + j) * Mp + a];
+    }
+    for (int j = 0; j < 2; ++j) {
+      const double sj = j == 0 ? 1.0 : -1.0;
+      Mat PA = matmul(Phi, Ap[j], Nfp, Mp, Np);
+      Mat YR = matmul(matmul(PA, DrM, Nfp, Np, Np), Ak[j], Nfp, Np, Mp);
+      Mat YS = matmul(matmul(PA, DsM, Nfp, Np, Np), Ak[j], Nfp, Np, Mp);
+      for (auto& y : YR) y *= sj;
+      for (auto& y : YS) y *= sj;
+      for (int k = 0; k < 2; ++k) {
+        o->ZR[j][k] = matmul(matmul(YR, Ap[k], Nfp, Mp, Np), o->Vinv, Nfp, Np, Np);
+        o->ZS[j][k] = matmul(matmul(YS, Ap[k], Nfp, Mp, Np), o->Vinv, Nfp, Np, Np);
+      }
+    }
+  }
   // reconstruction of the constant 1 on one side (0 on the other), evaluated on the diagonal
   {
     Mat ones(Np, 1.0);

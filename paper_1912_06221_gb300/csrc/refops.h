@@ -42,6 +42,11 @@ struct RefOps {
   // X[k][m][.][rho][.] = Q^rho_k C_m Vinv (Q^R = QRV, Q^S = QSV), layout
   // [m][Nfp][2][Np] per side.
   std::vector<double> X[2];
+  // Algorithm 1 (n . RDG(D_1 grad u~^1, D_2 grad u~^2), Separation = L2 projection onto the
+  // sub-triangles): the edge gradient is sum_j D_j (kappa_R ZR[j][k] + kappa_S ZS[j][k]) u_k,rot
+  // summed over input sides k, with ZR[j][k] = Y^R_j A+_k Vinv, Y^R_j = s_j Phi_diag A+_j
+  // (Vinv Dr V) A_j (s_1 = 1, s_2 = -1 for side 2's reflected frame), [Nfp][Np] each.
+  std::vector<double> ZR[2][2], ZS[2][2];
   std::vector<int> hyp;              // [Nfp] rotated-order indices of the shared face's nodes
 };
 

@@ -53,6 +53,12 @@ std::vector<double> pack_setup_refs(const RefOps& o) {
       aold = anew;
     }
   }
+  // Algorithm 1 factors per input side k: ZR[0][k], ZS[0][k] (weight D1), ZR[1][k], ZS[1][k] (D2)
+  for (int k = 0; k < 2; ++k)
+    for (int j = 0; j < 2; ++j) {
+      v.insert(v.end(), o.ZR[j][k].begin(), o.ZR[j][k].end());
+      v.insert(v.end(), o.ZS[j][k].begin(), o.ZS[j][k].end());
+    }
   (void)Np;
   return v;
 }
@@ -155,13 +161,13 @@ __device__ void simplex_basis_tab(double r, double s, const double* jac, double*
 // once per block in shared memory, plus NP^2 + 2 Nfp NP doubles per warp (under 48 KB).
 template <int N>
 __host__ __device__ constexpr int setup_warps() {
-  return N >= 6 ? 3 : 4;
+  return N >= 6 ? 2 : 4;
 }
 
 template <int N>
 __host__ __device__ constexpr int setup_ref_count() {
   constexpr int NP = np_of(N), NFP = nfp_of(N);
-  return 2 * NP + NP * NP + 4 * NFP * NP + 3 * NP + 3 * NFP + 2 * NFP + 3 * N * (N + 2);
+  return 2 * NP + NP * NP + 4 * NFP * NP + 3 * NP + 3 * NFP + 2 * NFP + 3 * N * (N + 2) + 8 * NFP * NP;
 }
 
 // One warp per edge: the parallelogram apex, the two rotated frames and the metric (lane
@@ -188,6 +194,7 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   const double* fmask = perminv + 3 * NP;
   const double* dvec = fmask + 3 * NFP;
   const double* jac = dvec + 2 * NFP;
+  const double* zq = jac + 3 * N * (N + 2);   // Algorithm 1 factors, 4 Nfp x Np per input side
 
   const int fa[3] = {0, 1, 2}, fb[3] = {1, 2, 0}, fc[3] = {2, 0, 1};
   const int k1 = in.k1[e], f1 = in.f1[e];
@@ -260,7 +267,14 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
     }
     const double* QRV = QV + (2 * side) * NFP * NP;
     const double* QSV = QV + (2 * side + 1) * NFP * NP;
-    for (int t = lane; t < NFP * NP; t += 32) sK[warp][t] = kR * QRV[t] + kS * QSV[t];
+    if (in.iface == RDG_IFACE_ALG1) {
+      // Algorithm 1: D_1 (kR ZR[0] + kS ZS[0]) + D_2 (kR ZR[1] + kS ZS[1]) for this side
+      const double* Z = zq + side * 4 * NFP * NP;
+      for (int t = lane; t < NFP * NP; t += 32)
+        sK[warp][t] = D1v * (kR * Z[t] + kS * Z[NFP * NP + t]) + D2v * (kR * Z[2 * NFP * NP + t] + kS * Z[3 * NFP * NP + t]);
+    } else {
+      for (int t = lane; t < NFP * NP; t += 32) sK[warp][t] = kR * QRV[t] + kS * QSV[t];
+    }
     __syncwarp();
     for (int t = lane; t < NFP * NP; t += 32) {
       const int i = t / NP, j = t % NP;
@@ -277,8 +291,9 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
 #pragma unroll 7
       for (int j = 0; j < NP; ++j) c = fma(sB[warp][i * NP + j], Vinv[j * NP + l], c);
       const int col = (int)perminv[f * NP + l];
-      const double Dt = in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
-                                                       : D1v * dvec[i] + D2v * dvec[NFP + i];
+      const double Dt = in.iface == RDG_IFACE_ALG1       ? 1.0   // D inside the factors
+                        : in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
+                                                         : D1v * dvec[i] + D2v * dvec[NFP + i];
       double w = -Jf * Dt * c;
       if (side == 0 && vn >= 0 && col == (int)fmask[f1 * NFP + i]) w += Jf * vn;
       if (side == 1 && vn < 0 && col == (int)fmask[f2 * NFP + (NFP - 1 - i)]) w += Jf * vn;

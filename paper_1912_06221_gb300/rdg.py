@@ -19,7 +19,7 @@ RDG_OK, RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA, RDG_EMESH, RDG_ERANK, RDG_ETIMEOUT, R
 BC_PERIODIC, BC_DIRICHLET = 0, 1
 FP64, FP32, FP32_3XTF32 = 0, 1, 2
 TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
-IFACE_ALG2, IFACE_HARMONIC = 0, 1
+IFACE_ALG2, IFACE_HARMONIC, IFACE_ALG1 = 0, 1, 2
 ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
 
 # symbol -> (restype, argtypes)

@@ -274,11 +274,12 @@ def test_repeatable_at_scale(prec):
 
 def test_manufactured_dirichlet_precision_sweep():
     """N = 3 manufactured solution with Dirichlet ghosts (sources and ghost data in time), run
-    to T = 2^-10 in FP64 and FP32 on 4x4x2 .. 16x16x2 meshes: each GPU state matches the
-    oracle's (FP64 1e-10, FP32 1e-5 normwise) and each mode converges at order ~4 in L2."""
+    to T = 2^-10 in FP64, FP32 and FP32 with the split-3xTF32 GEMM form on 4x4x2 .. 16x16x2
+    meshes: each GPU state matches the oracle's (FP64 1e-10, FP32 and 3xTF32 1e-5 normwise)
+    and each mode converges at order ~4 in L2."""
     from synth import manufactured_dirichlet
     from oracle.rhs import error_norms
-    errs = {rdg.FP64: [], rdg.FP32: []}
+    errs = {rdg.FP64: [], rdg.FP32: [], rdg.FP32_3XTF32: []}
     for mm in (4, 8, 16):
         w = manufactured_dirichlet(mm, N=3)
         me = Mesh(w.xy, w.tri, w.N, bc=DIRICHLET)
@@ -289,7 +290,7 @@ def test_manufactured_dirichlet_precision_sweep():
         n = int(math.ceil(T / dt))
         dt = T / n
         want = pr.solve(w.exact(me.x, me.y, 0.0), 0.0, dt, n)
-        for prec in (rdg.FP64, rdg.FP32):
+        for prec in (rdg.FP64, rdg.FP32, rdg.FP32_3XTF32):
             s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, bc=rdg.BC_DIRICHLET, period=None, precision=prec)
             xyn = s.node_coords()
             gxy = s.ghost_coords()
