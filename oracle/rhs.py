@@ -29,6 +29,25 @@ from .mesh import FACE_VERTS, Mesh
 from .refops import psi, triangle_quadrature
 
 
+# Published coefficients of the five-stage fourth-order 2N-storage Runge-Kutta scheme
+# (Carpenter and Kennedy 1994, solution 3), the integrator of the paper's Sec. 5.
+LSRK_A = (0.0,
+          -567301805773.0 / 1357537059087.0,
+          -2404267990393.0 / 2016746695238.0,
+          -3550918686646.0 / 2091501179385.0,
+          -1275806237668.0 / 842570457699.0)
+LSRK_B = (1432997174477.0 / 9575080441755.0,
+          5161836677717.0 / 13612068292357.0,
+          1720146321549.0 / 2090206949498.0,
+          3134564353537.0 / 4481467310338.0,
+          2277821191437.0 / 14882151754819.0)
+LSRK_C = (0.0,
+          1432997174477.0 / 9575080441755.0,
+          2526269341429.0 / 6820363962896.0,
+          2006345519317.0 / 3224310063776.0,
+          2802321613138.0 / 2924317926251.0)
+
+
 class Problem:
     """A mesh plus coefficients: D per element, constant velocity v, optional separable
     source and Dirichlet ghost data (lists of (nodal profile, kind, omega)).
@@ -136,9 +155,20 @@ class Problem:
         u2 = 0.75 * u + 0.25 * (u1 + dt * self.rhs(u1, t + dt))
         return u / 3.0 + 2.0 / 3.0 * (u2 + dt * self.rhs(u2, t + 0.5 * dt))
 
-    def solve(self, u, t0, dt, nsteps):
+    def lsrk_step(self, u, t, dt):
+        """One step of the five-stage fourth-order low-storage Runge-Kutta scheme the paper
+        uses (Sec. 5, Carpenter and Kennedy 1994), in its two-register form: for stage i,
+        du = a_i du + dt L(u, t + c_i dt), u = u + b_i du."""
+        du = np.zeros_like(u)
+        for a, b, c in zip(LSRK_A, LSRK_B, LSRK_C):
+            du = a * du + dt * self.rhs(u, t + c * dt)
+            u = u + b * du
+        return u
+
+    def solve(self, u, t0, dt, nsteps, scheme="ssp3"):
+        step = self.rk3_step if scheme == "ssp3" else self.lsrk_step
         for n in range(nsteps):
-            u = self.rk3_step(u, t0 + n * dt, dt)
+            u = step(u, t0 + n * dt, dt)
         return u
 
     def dense_operator(self):

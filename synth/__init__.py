@@ -153,6 +153,44 @@ def manufactured_dirichlet(m: int, N: int = 3, seed: int = 10, D: float = 1.0, T
                     source=src, ghost=ghost, exact=exact, meta={"T": T})
 
 
+def gaussian_exact(x0, y0, a=(0.0, 0.0), D=1.0, D0=2.0, M=1.0, period=(10.0, 10.0), images=2):
+    """Mass M loaded at (x0, y0) at t = -D0/D, diffusing with D and carried by a, on the
+    periodic domain: the free-space solution M/(4 pi (D t + D0)) exp(-|x - x0 - a t|^2 /
+    (4 (D t + D0))) summed over the periodic images within `images` periods (the next ones
+    are below 1e-25 for the paper's D0 = 2 and a 10-wide domain)."""
+    def f(x, y, t):
+        s = D * t + D0
+        out = np.zeros(np.broadcast(x, y).shape)
+        cx, cy = x0 + a[0] * t, y0 + a[1] * t
+        for i in range(-images, images + 1):
+            for j in range(-images, images + 1):
+                dx = x - cx - i * period[0]
+                dy = y - cy - j * period[1]
+                out = out + np.exp(-(dx * dx + dy * dy) / (4 * s))
+        return M / (4 * np.pi * s) * out
+    return f
+
+
+def paper_gaussian(m: int, N: int, advection: bool = False, jitter: float = 0.0, seed: int = 0, T: float = 0.5):
+    """The paper's verification problems (Sec. 5.1 diffusion, Sec. 5.2 advection-diffusion),
+    on stand-ins for its grid a: the 10 x 10 square [0, 10] x [-5, 5] cut into m x m cells
+    split by "/" diagonals (each triangle pair a parallelogram, as in grid a; jitter > 0
+    moves interior vertices so the reconstruction truncates areas, in the spirit of grids
+    b and c), periodic, D = 1, D0 = 2, M = 1; diffusion: (x0, y0) = (5, 0), a = 0;
+    advection-diffusion: (x0, y0) = (4, -1), a = (6, 6).  Final time 0.5."""
+    xy, tri = unit_square_mesh(m, jitter, seed)
+    xy = xy * 10.0
+    xy[:, 1] -= 5.0
+    if advection:
+        x0, y0, a = 4.0, -1.0, (6.0, 6.0)
+    else:
+        x0, y0, a = 5.0, 0.0, (0.0, 0.0)
+    exact = gaussian_exact(x0, y0, a)
+    return Workload("%s_N%d_m%d" % ("advdiff" if advection else "diffusion", N, m), N, m, xy, tri, PERIODIC,
+                    np.ones(tri.shape[0]), a, lambda x, y: exact(x, y, 0.0), steps=0, period=(10.0, 10.0),
+                    exact=exact, meta={"T": T})
+
+
 def fourier_u0(seed: int, kmax: int = 3):
     """Random low-mode periodic field sum_{|kx|,|ky|<=kmax} a_k {sin,cos}, a_k ~ N(0,1)/(1+|k|^2)."""
     rng = np.random.default_rng(seed)
