@@ -142,3 +142,22 @@ def test_mutation_alg1_side2_gradient_not_reflected(monkeypatch):
         return out
     monkeypatch.setattr(ardg.EdgeOps, "flux_algorithm1", bad)
     _fails(T1.test_alg1_exact_for_global_polynomials, 2)
+
+
+def test_mutation_lsrk_stage_time(monkeypatch):
+    """A wrong stage time in the low-storage Runge-Kutta step (the third stage evaluated at
+    the second stage's time)."""
+    from tests import test_oracle_lsrk as TL
+    bad = list(orhs.LSRK_C)
+    bad[2] = bad[1]
+    monkeypatch.setattr(orhs, "LSRK_C", tuple(bad))
+    _fails(TL.test_lsrk_integrates_cubics_in_time_exactly)
+
+
+def test_mutation_lsrk_weight(monkeypatch):
+    """A wrong stage weight (the last two b_i swapped)."""
+    from tests import test_oracle_lsrk as TL
+    bad = list(orhs.LSRK_B)
+    bad[3], bad[4] = bad[4], bad[3]
+    monkeypatch.setattr(orhs, "LSRK_B", tuple(bad))
+    _fails(TL.test_lsrk_local_error_is_fifth_order)
