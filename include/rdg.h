@@ -159,11 +159,19 @@ int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
  * has no counterpart to this entry point. */
 int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
 
-/* One SSP-RK3 step of the resident state from time t with step dt (stages at t, t+dt,
- * t+dt/2); enqueued, no host synchronisation. */
+/* Time integrator of rdg_rk_step, rdg_solve_to_time and batch steps:
+ * RDG_INTEGRATOR_SSP_RK3 (default) three-stage SSP-RK3, stages at t, t+dt, t+dt/2;
+ * RDG_INTEGRATOR_LSRK54 the five-stage fourth-order low-storage scheme of Carpenter and
+ * Kennedy (1994) that the paper's results use (Sec. 5), in its two-register form (the state
+ * and one residual).  Errors: RDG_EINVAL for another value. */
+enum { RDG_INTEGRATOR_SSP_RK3 = 0, RDG_INTEGRATOR_LSRK54 = 1 };
+int rdg_set_integrator(rdg_ctx* ctx, int integrator);
+
+/* One step of the resident state from time t with step dt with the selected integrator;
+ * enqueued, no host synchronisation. */
 int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
 
-/* nsteps SSP-RK3 steps of the resident state from t0 with step dt, replayed from a CUDA
+/* nsteps steps of the selected integrator from t0 with step dt, replayed from a CUDA
  * graph of a fixed chunk of steps (captured on first use for a given dt); enqueued. */
 int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps);
 

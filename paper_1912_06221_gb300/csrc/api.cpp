@@ -708,13 +708,14 @@ int64_t keep_tiles(const rdg_ctx* ctx) {
 }
 
 template <typename T>
-int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta) {
+int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta,
+                  void* out2 = nullptr, T rka = T(0), T rkb = T(0)) {
   EdgeArgs<T> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const T*)us, (T*)ctx->d_flux, (const T*)ctx->d_G,
                  ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, (T*)ctx->d_vol,
                  (const T*)ctx->d_geo, ctx->d_f12, (T*)ctx->d_fb, keep_tiles(ctx)};
   ElemArgs<T> la{(const T*)us, (const T*)un, (T*)out, (const T*)ctx->d_flux, ctx->d_eref, (const T*)ctx->d_geo,
                  (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta, ctx->d_err, ctx->E, (const T*)ctx->d_vol,
-                 (const T*)ctx->d_fb};
+                 (const T*)ctx->d_fb, (T*)out2, rka, rkb};
   const bool prof = ctx->prof && !ctx->capturing;
   cudaStream_t st = ls(ctx);
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -740,7 +741,31 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
   return rc;
 }
 
+// Five-stage fourth-order low-storage Runge-Kutta scheme (Carpenter and Kennedy 1994, the
+// integrator of the paper's Sec. 5): published coefficients a_i, b_i and stage times c_i.
+constexpr double kLsrkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                              -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+constexpr double kLsrkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                              1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                              2277821191437.0 / 14882151754819.0};
+constexpr double kLsrkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                              2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+template <typename T>
+int enqueue_lsrk_step(rdg_ctx* ctx, const TimeArg& base, double dt) {
+  // two registers: u (d_u) and the residual du (d_u1), both updated in place per stage
+  int rc = RDG_OK;
+  for (int i = 0; i < 5 && rc == RDG_OK; ++i) {
+    TimeArg ti = base;
+    ti.off = base.off + kLsrkC[i];
+    rc = enqueue_stage<T>(ctx, ctx->d_u, ctx->d_u1, ctx->d_u, 4, (T)dt, ti, ctx->d_u1, (T)kLsrkA[i], (T)kLsrkB[i]);
+  }
+  return rc;
+}
+
 int enqueue_rk_step(rdg_ctx* ctx, const TimeArg& base, double dt) {
+  if (ctx->integrator == RDG_INTEGRATOR_LSRK54)
+    return ctx->esz == 4 ? enqueue_lsrk_step<float>(ctx, base, dt) : enqueue_lsrk_step<double>(ctx, base, dt);
   // stage times t, t + dt, t + dt/2 (as offsets in units of dt)
   TimeArg t1 = base, t2 = base, t3 = base;
   t2.off = base.off + 1.0;
@@ -845,6 +870,16 @@ int rdg_solve_to_time(rdg_ctx* ctx, double t0, double dt, int64_t nsteps) {
     int rc = enqueue_rk_step(ctx, ta, dt);
     if (rc != RDG_OK) return fail(ctx, rc, "kernel launch failed");
   }
+  return RDG_OK;
+}
+
+int rdg_set_integrator(rdg_ctx* ctx, int integrator) {
+  if (!ctx) return RDG_EINVAL;
+  if (integrator != RDG_INTEGRATOR_SSP_RK3 && integrator != RDG_INTEGRATOR_LSRK54)
+    return fail(ctx, RDG_EINVAL, "integrator must be RDG_INTEGRATOR_SSP_RK3 or RDG_INTEGRATOR_LSRK54");
+  ctx->integrator = integrator;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
   return RDG_OK;
 }
 

@@ -35,6 +35,7 @@ struct rdg_ctx {
   double vx = 0, vy = 0;
   std::vector<double> Dk;
   // device buffers
+  int integrator = RDG_INTEGRATOR_SSP_RK3;
   bool gemm = false;                // GEMM form of the edge flux (RDG_FP32_3XTF32, N <= kMaxGemmN)
   void* d_W = nullptr;              // tiled per-edge operators, or the GEMM-form parameter records
   int32_t *d_k1 = nullptr, *d_k2 = nullptr, *d_eref = nullptr;

@@ -81,9 +81,13 @@ struct ElemArgs {
   int64_t E;           // edges (for the index self-check)
   const T* vol;        // fused form: precomputed volume term [K][Np] (else null)
   const T* fb;         // fused form: face fluxes [K][3][Nfp]
+  // low-storage Runge-Kutta stage (mode 4): un is the residual register du (read only when
+  // rka != 0), du' = rka du + dt L(us) is written to out2 and us + rkb du' to out
+  T* out2;
+  T rka, rkb;
 };
 
-// mode: 0 rhs only; 1..3 the three SSP-RK3 stage combinations
+// mode: 0 rhs only; 1..3 the three SSP-RK3 stage combinations; 4 a low-storage RK stage
 int launch_edge32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 int launch_edge64(int N, const EdgeArgs<double>& a, cudaStream_t s);
 int launch_elem32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s);

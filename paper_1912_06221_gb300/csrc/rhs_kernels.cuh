@@ -452,11 +452,11 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
     gv.load(a.vol + k0 * NP, nk * NP);
     gq.load(a.fb + k0 * NQ, nk * NQ);
     if (MODE >= 1) gs.load(a.us + k0 * NP, nk * NP);
-    if (MODE >= 2) gn.load(a.un + k0 * NP, nk * NP);
+    if (MODE == 2 || MODE == 3 || (MODE == 4 && a.rka != T(0))) gn.load(a.un + k0 * NP, nk * NP);
     gv.store(shv, nk * NP);
     gq.store(shq, nk * NQ);
     if (MODE >= 1) gs.store(shs, nk * NP);
-    if (MODE >= 2) gn.store(shn, nk * NP);
+    if (MODE == 2 || MODE == 3 || (MODE == 4 && a.rka != T(0))) gn.store(shn, nk * NP);
   }
   const T ij = active ? a.geo[5 * a.K + k] : T(0);
   if (tid < a.frc.nsrc) tau_s[tid] = (T)tau_of(a.frc.kind[tid], a.frc.omega[tid], stage_time(a.time));
@@ -485,18 +485,42 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
       for (int i = 0; i < NP; ++i) rhs[i] = fma(tau_s[m], S[i], rhs[i]);
     }
   }
+  if constexpr (MODE == 4) {
+    // low-storage stage: du' = rka du + dt L, u' = u + rkb du' (both rows written in place)
+    const bool rd = a.rka != T(0);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    if (MODE >= 1) rhs[i] = fma(a.dt, rhs[i], shs[tid * NP + i]);
-    if (MODE >= 2) rhs[i] = rk_combine<T, MODE>(shn[tid * NP + i], rhs[i]);
-  }
-  __syncthreads();
-  if (active) {
+    for (int i = 0; i < NP; ++i) {
+      const T du = rd ? fma(a.rka, shn[tid * NP + i], a.dt * rhs[i]) : a.dt * rhs[i];
+      rhs[i] = du;
+    }
+    __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) shv[tid * NP + i] = rhs[i];
+      for (int i = 0; i < NP; ++i) shv[tid * NP + i] = fma(a.rkb, rhs[i], shs[tid * NP + i]);
+    }
+    __syncthreads();
+    stage_out(a.out + k0 * NP, shv, nk * NP);
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) shv[tid * NP + i] = rhs[i];
+    }
+    __syncthreads();
+    stage_out(a.out2 + k0 * NP, shv, nk * NP);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      if (MODE >= 1) rhs[i] = fma(a.dt, rhs[i], shs[tid * NP + i]);
+      if (MODE >= 2) rhs[i] = rk_combine<T, MODE>(shn[tid * NP + i], rhs[i]);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) shv[tid * NP + i] = rhs[i];
+    }
+    __syncthreads();
+    stage_out(a.out + k0 * NP, shv, nk * NP);
   }
-  __syncthreads();
-  stage_out(a.out + k0 * NP, shv, nk * NP);
 }
 
 }  // namespace dev
@@ -554,6 +578,7 @@ inline int launch_elem_t(int mode, const ElemArgs<T>& a, cudaStream_t s) {
       case 1: return launch_pdl(dev::elem_lite_kernel<T, N, 1>, g2, BLK, s, a);
       case 2: return launch_pdl(dev::elem_lite_kernel<T, N, 2>, g2, BLK, s, a);
       case 3: return launch_pdl(dev::elem_lite_kernel<T, N, 3>, g2, BLK, s, a);
+      case 4: return launch_pdl(dev::elem_lite_kernel<T, N, 4>, g2, BLK, s, a);
       default: return RDG_EINVAL;
     }
   } else {

@@ -20,6 +20,7 @@ BC_PERIODIC, BC_DIRICHLET = 0, 1
 FP64, FP32, FP32_3XTF32 = 0, 1, 2
 TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
 IFACE_ALG2, IFACE_HARMONIC, IFACE_ALG1 = 0, 1, 2
+SSP_RK3, LSRK54 = 0, 1
 ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
 
 # symbol -> (restype, argtypes)
@@ -52,6 +53,7 @@ SIGNATURES = {
     "rdg_query_bytes": (_INT, [_INT, _I64, _I64, _I64, _INT, _INT, _INT, ctypes.POINTER(_I64)]),
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
     "rdg_get_edge_operators": (_INT, [_P, _P, _P]),
+    "rdg_set_integrator": (_INT, [_P, _INT]),
     "rdg_batch_create": (_INT, [ctypes.POINTER(_P), _INT, _P, _INT]),
     "rdg_batch_destroy": (_INT, [_P]),
     "rdg_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -221,6 +223,10 @@ class Solver:
 
     def rk_step(self, t: float, dt: float):
         self._call("rdg_rk_step", float(t), float(dt))
+
+    def set_integrator(self, kind: int):
+        """SSP_RK3 (default) or LSRK54 (the paper's five-stage fourth-order scheme)."""
+        self._call("rdg_set_integrator", int(kind))
 
     def solve_to_time(self, t0: float, dt: float, nsteps: int):
         self._call("rdg_solve_to_time", float(t0), float(dt), int(nsteps))
