@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--serve-slots", type=int, default=32)
     p.add_argument("--serve-setup-workers", type=int, default=6)
     p.add_argument("--batch", action="store_true", help="run the batched uneven workload instead")
+    p.add_argument("--paper-problems", action="store_true",
+                   help="the paper's Gaussian diffusion / advection-diffusion convergence series instead")
+    p.add_argument("--sweep", action="store_true", help="the N=3 manufactured-solution precision sweep instead")
     p.add_argument("--batch-chunk", type=int, default=25)
     return p.parse_args()
 
@@ -493,12 +496,16 @@ def run_batch(args):
     import paper_1912_06221_gb300 as rdg
     from synth import batched_heat
     torch.cuda.set_device(0)
+    from paper_1912_06221_gb300 import autotune
     probs = batched_heat(seed=2)
     steps = probs[0].steps
     solvers, dts, u0s = [], [], []
+    t_tune = time.perf_counter()
+    choices = [autotune.choose_precision(w.xy, w.tri, w.N, w.D_elem, v=w.v) for w in probs]
+    t_tune = time.perf_counter() - t_tune
     t_setup = time.perf_counter()
-    for w in probs:
-        s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32)
+    for w, ch in zip(probs, choices):
+        s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=ch["precision"])
         xyn = s.node_coords()
         u0 = np.ascontiguousarray(w.u0(xyn[..., 0], xyn[..., 1]))
         rho = spectral_radius(s, torch, iters=30)
@@ -531,6 +538,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
+    chunk_tune = autotune.choose_chunk(bt, solvers, u0s, steps, candidates=(5, 10, 25, 50, 100))
     for _ in range(args.warmup):
         one(True)
         one(False)
@@ -547,6 +555,7 @@ def run_batch(args):
     for w, s, dt, u in zip(probs, solvers, dts, u0s):
         s64 = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP64)
         s64.set_state(u.double())
+        # (FP32 members are stepped by whichever FP32-accurate form the tuner picked)
         s64.solve_to_time(0.0, dt, steps)
         a64 = s64.get_state_host()
         s64.close()
@@ -559,16 +568,157 @@ def run_batch(args):
                                    "[1e-3,1], Fourier u0, 100 SSP-RK3 steps each, FP32",
                        "triangles_total": int(sum(s.K for s in solvers)),
                        "dof_total": int(sum(s.K * s.Np for s in solvers)),
-                       "orders": [int(w.N) for w in probs], "graph_chunk": args.batch_chunk,
+                       "orders": [int(w.N) for w in probs], "graph_chunk": chunk_tune["chunk"],
                        "l2_flush": "256 MB buffer written before each timed step (outside the events)"},
             "sequential": {"value": units / (ms_s / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms_s,
                            "note": "the same 64 solves one after another, each replaying its own graph"},
             "fp32_rel_l2_vs_fp64": {"max": max(errs), "median": float(np.median(errs))},
-            "setup_s": t_setup, "clocks": clocks}
+            "setup_s": t_setup, "clocks": clocks,
+            "autotune": {"seconds": t_tune,
+                         "precision_by_order_and_size_class": sorted(
+                             {(int(w.N), autotune.size_class(w.K), "fp32" if c["precision"] == rdg.FP32 else "fp32_3xtf32",
+                               json.dumps(c["ms"])) for w, c in zip(probs, choices)}),
+                         "graph_chunk_ms": chunk_tune["ms"]}}
     print(json.dumps(line), flush=True)
     bt.close()
     for s in solvers:
         s.close()
+
+
+def _gpu_rho(s, torch, iters=40):
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((s.K, s.Np), generator=g, device="cuda", dtype=s.dtype)
+    y = torch.empty_like(x)
+    for _ in range(iters):
+        x /= torch.linalg.vector_norm(x)
+        s.rhs_eval(x, y, 0.0)
+        x, y = y, x
+    return float(torch.linalg.vector_norm(x))
+
+
+def run_paper_problems(args):
+    """The paper's verification problems (Sec. 5.1 Gaussian diffusion, Sec. 5.2 Gaussian
+    advection-diffusion; D = 1, D0 = 2, t = 0.5) on stand-ins for its grid-a series (32 ..
+    8192 triangles, every triangle pair a parallelogram, periodic 10 x 10 square with the
+    image-sum exact solution), FP64 on the GPU with the paper's five-stage fourth-order
+    Runge-Kutta scheme at a time step fixed by the finest mesh.  Reports L2 / L_inf errors
+    (Eqs. L2_norm_cellUnit, Linf_norm_cellUnit), two-mesh orders, and the paper's Tables
+    purediff_ooa / adv_diff_ooa (grid a) beside them."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06221_gb300 as rdg
+    from synth import paper_gaussian
+    from oracle.mesh import Mesh            # error norms only (quadrature against the exact solution)
+    from oracle.rhs import error_norms
+    tables = {False: {1: 2.015, 2: 2.828, 3: 4.005}, True: {1: 1.690, 2: 2.629, 3: 3.970}}
+    ms = (4, 8, 16, 32, 64)
+    out = {}
+    t_start = time.perf_counter()
+    for adv in (False, True):
+        for N in (1, 2, 3):
+            wf = paper_gaussian(ms[-1], N, advection=adv)
+            s = rdg.Solver(wf.xy, wf.tri, N, wf.D_elem, v=wf.v, period=(10.0, 10.0), precision=rdg.FP64)
+            n = int(math.ceil(0.5 / (0.5 * 2.5127 / _gpu_rho(s, torch))))
+            s.close()
+            dt = 0.5 / n
+            l2, li = [], []
+            for m in ms:
+                w = paper_gaussian(m, N, advection=adv)
+                s = rdg.Solver(w.xy, w.tri, N, w.D_elem, v=w.v, period=(10.0, 10.0), precision=rdg.FP64)
+                s.set_integrator(rdg.LSRK54)
+                xyn = s.node_coords()
+                s.set_state(w.exact(xyn[..., 0], xyn[..., 1], 0.0))
+                s.solve_to_time(0.0, dt, n)
+                u = s.get_state_host()
+                s.synchronize()
+                s.close()
+                e2, ei = error_norms(Mesh(w.xy, w.tri, N, period=(10.0, 10.0)), u, w.exact, 0.5)
+                l2.append(e2)
+                li.append(ei)
+            key = "%s_P%d" % ("advection_diffusion" if adv else "diffusion", N)
+            out[key] = {"triangles": [2 * m * m for m in ms], "steps": n, "dt": dt, "l2": l2, "linf": li,
+                        "l2_orders": [math.log2(l2[i] / l2[i + 1]) for i in range(len(ms) - 1)],
+                        "linf_orders": [math.log2(li[i] / li[i + 1]) for i in range(len(ms) - 1)],
+                        "paper_table_l2_grid_a": tables[adv][N]}
+    line = {"metric": "observed order of accuracy, paper verification problems", "unit": "order",
+            "value": out["diffusion_P3"]["l2_orders"][-1], "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "integrator": "LSRK5(4)", "seconds": time.perf_counter() - t_start,
+            "config": {"workload": "Gaussian diffusion and advection-diffusion (D=1, D0=2, a=(6,6)), t=0.5, "
+                                   "grid-a series 32..8192 triangles, periodic 10x10"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    """N = 3 manufactured solution u = sin(pi x) sin(pi y) cos t (Dirichlet, D = 1) in FP64, FP32
+    and FP32 with the split-3xTF32 GEMM form.  Meshes 32^2..128^2 x 2 run to T = 2^-10 (L2 error
+    against the exact solution, orders); 256^2..1024^2 x 2 (up to 2.1M triangles) run 30 steps
+    at 0.5 x the stability bound (difference to the FP64 GPU state and throughput), since the
+    full T takes ~1e5..1e6 steps there."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06221_gb300 as rdg
+    from synth import manufactured_dirichlet
+    from oracle.mesh import Mesh            # error norms only
+    from oracle.rhs import error_norms
+    modes = (("fp64", rdg.FP64), ("fp32", rdg.FP32), ("fp32_3xtf32", rdg.FP32_3XTF32))
+    rows = []
+    for m in (32, 64, 128, 256, 512, 1024):
+        w = manufactured_dirichlet(m, N=3)
+        full = m <= 128
+        row = {"m": m, "triangles": 2 * m * m}
+        states = {}
+        for name, prec in modes:
+            s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, bc=rdg.BC_DIRICHLET, period=None, precision=prec)
+            xyn = s.node_coords()
+            gxy = s.ghost_coords()
+            s.set_forcing([(f(xyn[..., 0], xyn[..., 1]), k, o) for f, k, o in
+                           zip(w.source.funcs, w.source.kinds, w.source.omegas)],
+                          [(f(gxy[..., 0], gxy[..., 1]), k, o) for f, k, o in
+                           zip(w.ghost.funcs, w.ghost.kinds, w.ghost.omegas)])
+            if "dt" not in row:
+                rho = _gpu_rho(s, torch)
+                dt = 0.5 * 2.5127 / rho
+                T = w.meta["T"]
+                n = int(math.ceil(T / dt)) if full else 30
+                row["dt"] = T / n if full else dt
+                row["steps"] = n
+            u0 = np.ascontiguousarray(w.exact(xyn[..., 0], xyn[..., 1], 0.0), dtype=s.np_dtype)
+            s.set_state(u0)
+            s.solve_to_time(0.0, row["dt"], min(row["steps"], 16))
+            torch.cuda.synchronize()
+            s.set_state(u0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.solve_to_time(0.0, row["dt"], row["steps"])
+            b.record()
+            torch.cuda.synchronize()
+            ms_ = a.elapsed_time(b)
+            u = s.get_state_host().astype(np.float64)
+            s.synchronize()
+            row[name + "_gdof_per_s"] = s.K * s.Np * 3 * row["steps"] / (ms_ / 1e3) / 1e9
+            states[name] = u
+            if full:
+                e2, ei = error_norms(Mesh(w.xy, w.tri, w.N, bc=rdg.BC_DIRICHLET), u, w.exact, row["dt"] * row["steps"])
+                row[name + "_l2_err"] = e2
+                row[name + "_linf_err"] = ei
+            s.close()
+        for name in ("fp32", "fp32_3xtf32"):
+            d = states[name] - states["fp64"]
+            row[name + "_rel_l2_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(states["fp64"]))
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    for name, _ in modes:
+        e = [r[name + "_l2_err"] for r in rows if name + "_l2_err" in r]
+        for i, r in enumerate([r for r in rows if name + "_l2_err" in r][1:]):
+            r[name + "_l2_order"] = math.log2(e[i] / e[i + 1])
+    line = {"metric": "precision sweep, N=3 manufactured solution", "unit": "rel L2 / order / GDOF/s",
+            "value": rows[-1]["fp32_gdof_per_s"], "higher_is_better": True, "dtype": "f64/f32/3xtf32",
+            "data": "synthetic", "config": {"workload": "u = sin(pi x) sin(pi y) cos t, Dirichlet, D = 1, N = 3, "
+                                                        "meshes 32^2..1024^2 x 2, seed 10"}, "rows": rows}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
@@ -579,5 +729,9 @@ if __name__ == "__main__":
         run_serve(a)
     elif a.batch:
         run_batch(a)
+    elif a.paper_problems:
+        run_paper_problems(a)
+    elif a.sweep:
+        run_sweep(a)
     else:
         run_ours(a)

@@ -241,6 +241,9 @@ const char* rdg_batch_last_error(const rdg_batch* b);
 int rdg_batch_add(rdg_batch* b, rdg_ctx* ctx, double t0, double dt);
 /* Remove a member (waits for its branch); RDG_EINVAL if ctx is not a member. */
 int rdg_batch_remove(rdg_batch* b, rdg_ctx* ctx);
+/* Steps per captured graph from now on (1..1024; the graph is captured again on the next
+ * step).  RDG_EINVAL outside the range. */
+int rdg_batch_set_chunk(rdg_batch* b, int chunk);
 /* Number of members into *n. */
 int rdg_batch_size(const rdg_batch* b, int* n);
 /* Enqueue nsteps SSP-RK3 steps of every member: floor(nsteps/chunk) replays of the graph

@@ -204,6 +204,18 @@ int rdg_batch_remove(rdg_batch* b, rdg_ctx* ctx) {
   return bfail(b, RDG_EINVAL, "context is not in the batch");
 }
 
+int rdg_batch_set_chunk(rdg_batch* b, int chunk) {
+  if (!b) return RDG_EINVAL;
+  if (chunk < 1 || chunk > 1024) return bfail(b, RDG_EINVAL, "chunk must be in 1..1024");
+  if (chunk != b->chunk) {
+    DevGuard g(b->device);
+    cudaStreamSynchronize(b->stream);   // the replaced graph may still be running
+    drop_graph(b);
+    b->chunk = chunk;
+  }
+  return RDG_OK;
+}
+
 int rdg_batch_size(const rdg_batch* b, int* n) {
   if (!b || !n) return RDG_EINVAL;
   *n = (int)b->members.size();

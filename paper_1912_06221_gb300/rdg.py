@@ -60,6 +60,7 @@ SIGNATURES = {
     "rdg_batch_add": (_INT, [_P, _P, _D, _D]),
     "rdg_batch_remove": (_INT, [_P, _P]),
     "rdg_batch_size": (_INT, [_P, ctypes.POINTER(_INT)]),
+    "rdg_batch_set_chunk": (_INT, [_P, _INT]),
     "rdg_batch_step": (_INT, [_P, _I64]),
     "rdg_batch_synchronize": (_INT, [_P]),
 }
@@ -296,6 +297,10 @@ class Batch:
 
     def step(self, nsteps: int):
         self._call("rdg_batch_step", int(nsteps))
+
+    def set_chunk(self, chunk: int):
+        """Steps per replayed graph (the graph is captured again on the next step)."""
+        self._call("rdg_batch_set_chunk", int(chunk))
 
     def synchronize(self):
         self._call("rdg_batch_synchronize")

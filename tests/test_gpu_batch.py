@@ -171,3 +171,48 @@ def test_batch_errors():
     bt.close()
     s.close()
     s2.close()
+
+
+def test_batch_chunk_change_keeps_results():
+    """Replaying the same steps with another graph chunk gives the same states bit for bit."""
+    items = _build(MEMBERS[:3])
+    bt = rdg.Batch(chunk=16)
+    for (spec, a, b) in items:
+        bt.add(a[0], a[2])
+    bt.step(20)
+    bt.synchronize()
+    got = [a[0].get_state_host() for (_, a, _) in items]
+    for (spec, a, b) in items:
+        a[0].set_state(a[1])
+    bt.set_chunk(7)
+    with pytest.raises(rdg.RdgError):
+        bt.set_chunk(0)
+    bt2 = rdg.Batch(chunk=7)
+    for (spec, a, b) in items:
+        bt.remove(a[0])
+        bt2.add(a[0], a[2])
+    bt2.step(20)
+    bt2.synchronize()
+    for g, (spec, a, b) in zip(got, items):
+        if spec[5]:
+            assert relerr(a[0].get_state_host(), g) < (1e-13 if spec[2] == rdg.FP64 else 1e-6)
+        else:
+            assert np.array_equal(a[0].get_state_host(), g)
+    bt.close()
+    bt2.close()
+    for (spec, a, b) in items:
+        a[0].close()
+        b[0].close()
+
+
+def test_autotune_picks_a_valid_form_and_caches():
+    from paper_1912_06221_gb300 import autotune
+    xy, tri = unit_square_mesh(12, 0.1, 1)
+    D = np.full(tri.shape[0], 0.3)
+    c1 = autotune.choose_precision(xy, tri, 3, D)
+    assert c1["precision"] in (rdg.FP32, rdg.FP32_3XTF32) and not c1["cached"]
+    assert set(c1["ms"]) == {"fp32", "fp32_3xtf32"} and all(t > 0 for t in c1["ms"].values())
+    c2 = autotune.choose_precision(xy, tri, 3, D)
+    assert c2["cached"] and c2["precision"] == c1["precision"]
+    c6 = autotune.choose_precision(xy, tri, 6, D)
+    assert c6["precision"] == rdg.FP32 and set(c6["ms"]) == {"fp32"}
