@@ -84,35 +84,35 @@ __device__ __forceinline__ void report(int* err, int bit) {
 // metric-folded coefficients F_r = a_r u - (g_rr u_r + g_rs u_s), F_s = a_s u - (g_rs u_r +
 // g_ss u_s), vol = Wr F_r + Ws F_s (Wr = M^{-1} Dr^T M, Ws = M^{-1} Ds^T M).  The derivatives
 // are taken of u - u_0 (Dr, Ds annihilate constants), so the rounding of their large entries
-// multiplies differences of nearby values rather than u itself.
+// multiplies differences of nearby values rather than u itself.  Evaluated node by node as a
+// running outer product (F_r, F_s at node j, then their column j of Wr, Ws into vol), so only
+// u - u_0 and vol are live: 2 Np values instead of 5 Np.
 template <typename T, int N>
 __device__ __forceinline__ void volume_row(const T (&u)[np_of(N)], T ar, T as, T grr, T grs, T gss,
                                            T (&vol)[np_of(N)]) {
   constexpr int NP = np_of(N);
   constexpr int ODR = 0, ODS = NP * NP, OWR = 2 * NP * NP, OWS = 3 * NP * NP;
-  T fr[NP], fs[NP], du[NP];
+  T du[NP];
 #pragma unroll
   for (int j = 1; j < NP; ++j) du[j] = u[j] - u[0];
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
+  for (int i = 0; i < NP; ++i) vol[i] = T(0);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
     T ur = T(0), us = T(0);
 #pragma unroll
-    for (int j = 1; j < NP; ++j) {
-      ur = fma((T)RDG_TAB[ODR + i * NP + j], du[j], ur);
-      us = fma((T)RDG_TAB[ODS + i * NP + j], du[j], us);
+    for (int k = 1; k < NP; ++k) {
+      ur = fma((T)RDG_TAB[ODR + j * NP + k], du[k], ur);
+      us = fma((T)RDG_TAB[ODS + j * NP + k], du[k], us);
     }
-    fr[i] = ar * u[i] - (grr * ur + grs * us);
-    fs[i] = as * u[i] - (grs * ur + gss * us);
-  }
+    const T uj = j == 0 ? u[0] : du[j] + u[0];
+    const T fr = ar * uj - (grr * ur + grs * us);
+    const T fs = as * uj - (grs * ur + gss * us);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    T acc = T(0);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      acc = fma((T)RDG_TAB[OWR + i * NP + j], fr[j], acc);
-      acc = fma((T)RDG_TAB[OWS + i * NP + j], fs[j], acc);
+    for (int i = 0; i < NP; ++i) {
+      vol[i] = fma((T)RDG_TAB[OWR + i * NP + j], fr, vol[i]);
+      vol[i] = fma((T)RDG_TAB[OWS + i * NP + j], fs, vol[i]);
     }
-    vol[i] = acc;
   }
 }
 
@@ -296,19 +296,22 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
 // evenly over the grid (block b is a volume block when floor((b+1) nv / nb) steps up), so
 // the volume FMAs run on the same SMs while the operator stream keeps HBM busy.
 // Resident stage blocks per SM asked of the compiler (FP32: 5 blocks up to N = 4, <= 102
-// registers; 4 above; FP64: 4 up to N = 3, 3 above), so the operator stream keeps enough
-// loads in flight.
+// registers; 6 above, where more warps in flight measured faster than more registers per
+// thread; FP64: 4 up to N = 3, 3 above), so the operator stream keeps enough loads in flight.
 template <typename T, int N>
 constexpr int stage_min_blocks() {
-  return sizeof(T) == 4 ? (N <= 4 ? 5 : 4) : (N <= 3 ? 4 : 3);
+  return sizeof(T) == 4 ? (N <= 4 ? 5 : 6) : (N <= 3 ? 4 : 3);
 }
 
-template <typename T, int N, bool VOL>
+// Operator stream kinds: 0 edge blocks only, fluxes to the per-edge buffer (allocation-free
+// entry point); 1 the fused form (edge and volume blocks interleaved, fluxes to the face
+// slots).
+template <typename T, int N, int KIND>
 __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_flux_kernel(EdgeArgs<T> a) {
   constexpr int NP = np_of(N);
   wait_for_predecessor();
   int64_t eblk = blockIdx.x;
-  if constexpr (VOL) {
+  if constexpr (KIND == 1) {
     __shared__ __align__(16) T sh[kStageBlock * NP];
     const int64_t nb = gridDim.x;
     const int64_t nv = (a.K + kStageBlock - 1) / kStageBlock;
@@ -321,8 +324,9 @@ __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_fl
     eblk = b - v1;    // edge blocks so far = blocks so far minus volume blocks so far
   }
   const int64_t e = eblk * kStageBlock + threadIdx.x;
-  if (e < a.E) stage_edge<T, N, VOL>(a, e);
+  if (e < a.E) stage_edge<T, N, KIND != 0>(a, e);
 }
+
 
 // Resident blocks per SM asked of the compiler for the surface-only form (VOLIN): FP32 orders
 // up to 4 fit 7 blocks of 128 threads (<= 73 registers), so a 131072-element stage (1024
@@ -559,10 +563,9 @@ inline int sm_count() {
 template <typename T, int N, bool VOL = false>
 inline int launch_edge_t(const EdgeArgs<T>& a, cudaStream_t s) {
   if (a.E == 0 && (!VOL || a.K == 0)) return RDG_OK;
-  int64_t grid = (a.E + kStageBlock - 1) / kStageBlock;
-  if (VOL) grid += (a.K + kStageBlock - 1) / kStageBlock;
-  if constexpr (VOL) return launch_pdl(dev::edge_flux_kernel<T, N, VOL>, (unsigned)grid, kStageBlock, s, a);
-  dev::edge_flux_kernel<T, N, VOL><<<(unsigned)grid, kStageBlock, 0, s>>>(a);
+  const int64_t ge = (a.E + kStageBlock - 1) / kStageBlock, gv = (a.K + kStageBlock - 1) / kStageBlock;
+  if constexpr (VOL) return launch_pdl(dev::edge_flux_kernel<T, N, 1>, (unsigned)(ge + gv), kStageBlock, s, a);
+  dev::edge_flux_kernel<T, N, 0><<<(unsigned)ge, kStageBlock, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
 
