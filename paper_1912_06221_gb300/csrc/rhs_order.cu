@@ -20,8 +20,13 @@ constexpr int kN = RDG_ORDER;
 constexpr int kNp = (kN + 1) * (kN + 2) / 2;
 constexpr int kTabN = 4 * kNp * kNp + 3 * kNp * (kN + 1);
 __constant__ RDG_REAL c_tab[kTabN];
+// the volume matrices again, in global memory, for the orders whose volume role stages them
+// in shared memory (layout of VolTab in rhs_kernels.cuh)
+constexpr int kNpp = (kNp * (int)sizeof(RDG_REAL) + 15) / 16 * 16 / (int)sizeof(RDG_REAL);
+__device__ __align__(16) RDG_REAL g_voltab[4 * kNp * kNpp];
 }  // namespace
 #define RDG_TAB c_tab
+#define RDG_VOLTAB g_voltab
 #include "rhs_kernels.cuh"
 
 // FP32 objects of orders 1..kMaxGemmN also hold the GEMM form of the edge flux.
@@ -43,6 +48,19 @@ int RDG_CAT(upload_tab_, RDG_CAT(RDG_TAG, RDG_ORDER))() {
   std::vector<RDG_REAL> t = pack_elem_table<RDG_REAL>(kN);
   if ((int)t.size() != kTabN) return RDG_EINVAL;
   if (cudaMemcpyToSymbol(c_tab, t.data(), t.size() * sizeof(RDG_REAL)) != cudaSuccess) return RDG_ECUDA;
+  {
+    // Dr, Ds row-major and Wr^T, Ws^T, rows padded to kNpp
+    std::vector<RDG_REAL> vt(4 * kNp * kNpp, RDG_REAL(0));
+    const int n2 = kNp * kNp;
+    for (int r = 0; r < kNp; ++r)
+      for (int c = 0; c < kNp; ++c) {
+        vt[r * kNpp + c] = t[r * kNp + c];
+        vt[kNp * kNpp + r * kNpp + c] = t[n2 + r * kNp + c];
+        vt[2 * kNp * kNpp + r * kNpp + c] = t[2 * n2 + c * kNp + r];
+        vt[3 * kNp * kNpp + r * kNpp + c] = t[3 * n2 + c * kNp + r];
+      }
+    if (cudaMemcpyToSymbol(g_voltab, vt.data(), vt.size() * sizeof(RDG_REAL)) != cudaSuccess) return RDG_ECUDA;
+  }
 #if RDG_GEMM
   const RefOps* o = get_refops(kN, nullptr);
   if (!o) return RDG_EINVAL;
