@@ -337,13 +337,14 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_t = []
-    out_host = np.empty_like(u0_host)
+    in_pinned = torch.from_numpy(u0_host).pin_memory()       # inputs in pinned host memory
+    out_pinned = torch.empty_like(in_pinned).pin_memory()
     for i in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.set_state(u0_host)
+        s.set_state(in_pinned)                  # host -> device copy of the step's input
         s.solve_to_time(0.0, dt, nrk)
-        out_host[...] = s.get_state_host()
+        s.get_state(out_pinned)                 # device -> host copy of the result (waits for it)
         e2e_t.append(time.perf_counter() - t0)
     e2e_val = s.K * s.Np * 3 * nrk * world / (float(np.mean(e2e_t))) / 1e9
 
@@ -425,7 +426,7 @@ def run_ours(args):
             "config": workload_config(args), "dt": dt, "rho": rho,
             "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
-                    "d2h_bytes_per_step": int(out_host.nbytes)},
+                    "d2h_bytes_per_step": int(out_pinned.numel() * out_pinned.element_size())},
             "gpu_launches": per_solve * args.steps,
             "fp64_gpu": fp64, "fp32_3xtf32": tf32}
     if rank == 0:

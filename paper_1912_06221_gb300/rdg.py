@@ -201,17 +201,30 @@ class Solver:
     def new_field(self):
         return self.torch.zeros((self.K, self.Np), dtype=self.dtype, device="cuda:%d" % self.device)
 
+    def _host_tensor(self, t):
+        torch = self.torch
+        if not (t.dtype == self.dtype and t.is_contiguous() and t.numel() == self.K * self.Np):
+            raise ValueError("expected a contiguous host %s tensor of %d values" % (self.dtype, self.K * self.Np))
+        return _P(t.data_ptr())
+
     def set_state(self, u):
+        """From a NumPy array or a host tensor (pinned memory copies fastest), or a CUDA tensor."""
         if isinstance(u, np.ndarray):
             a = np.ascontiguousarray(u, self.np_dtype)
             self._call("rdg_set_state", _ptr(a), 0)
+        elif not u.is_cuda:
+            self._call("rdg_set_state", self._host_tensor(u), 0)
         else:
             self._call("rdg_set_state", self._dev_tensor(u), 1)
 
     def get_state(self, out=None):
+        """Into `out`: a CUDA tensor (a new one if None) or a host tensor (e.g. pinned)."""
         if out is None:
             out = self.new_field()
-        self._call("rdg_get_state", self._dev_tensor(out), 1)
+        if out.is_cuda:
+            self._call("rdg_get_state", self._dev_tensor(out), 1)
+        else:
+            self._call("rdg_get_state", self._host_tensor(out), 0)
         return out
 
     def get_state_host(self):

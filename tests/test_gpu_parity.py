@@ -308,3 +308,17 @@ def test_manufactured_dirichlet_precision_sweep():
     for prec in errs:
         order = math.log2(errs[prec][1] / errs[prec][2])
         assert 3.5 < order < 4.5, (prec, errs[prec])
+
+
+@pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
+def test_state_round_trip_through_host_tensors(prec):
+    """set_state/get_state with (pinned) host tensors copy exactly what the NumPy path does."""
+    s, me, D = _setup(3, prec=prec, m=5)
+    u = random_nodal(s.K, s.Np, 21).astype(s.np_dtype)
+    pinned = torch.from_numpy(u.copy()).pin_memory()
+    s.set_state(pinned)
+    out = torch.empty_like(pinned).pin_memory()
+    s.get_state(out)
+    assert np.array_equal(out.numpy(), u)
+    assert np.array_equal(s.get_state_host(), u)
+    s.close()
