@@ -308,7 +308,8 @@ def run_ours(args):
     E, K, Np, Nfp = s.E, s.K, s.Np, s.Nfp
     # fused edge kernel: operator stream, edge ids, flux write, stage input (read once),
     # volume-term write, five element coefficients
-    edge_bytes = E * (Nfp * 2 * Np * 4 + 8 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
+    # (stored operator: Nfp (2 Np - 1) + 1 values per edge, the row sum stored once)
+    edge_bytes = E * ((Nfp * (2 * Np - 1) + 1) * 4 + 8 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
     if gemm:   # parameter records (16-byte words) instead of operators, plus the face-pair word
         edge_bytes = E * (((2 * Np + Nfp + 3 + 3) // 4) * 16 + 12 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
     # surface/stage kernel, averaged over the three stages (the step start is read in two):

@@ -15,9 +15,14 @@ constexpr int kTile = 32;            // edges per W tile (one warp, one edge per
 constexpr int kElemBlock = 128;      // elements per element-kernel block
 constexpr int kStageBlock = 128;     // threads per block of the stage (edge/volume) kernel
 
+// Stored values of one edge's flux operator in its difference form: per row, side 1's
+// columns 1..Np-1 and side 2's Np columns (2 Np - 1 values), then the one value J_f (v.n1)
+// that every row's column 0 (the row sum) would hold.
+inline int w_stored_values(int N) { return nfp_of(N) * (2 * np_of(N) - 1) + 1; }
+
 // Words (of 16 bytes) per edge row block of the tiled flux operator.
 inline int w_vecs_per_edge(int N, int elem_bytes) {
-  int nw = nfp_of(N) * 2 * np_of(N);
+  int nw = w_stored_values(N);
   int per = 16 / elem_bytes;
   return (nw + per - 1) / per;
 }

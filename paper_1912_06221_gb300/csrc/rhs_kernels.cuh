@@ -273,10 +273,11 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
 // reads 512 contiguous bytes per load of its tile).
 template <typename T, int N, bool FB>
 __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
-  constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP;
+  constexpr int NP = np_of(N), NFP = nfp_of(N);
+  constexpr int RW = 2 * NP - 1, NWS = NFP * RW + 1;   // stored values per row / per edge
   using V = Vec16<T>;
   using VT = typename V::type;
-  constexpr int QW = (NW + V::n - 1) / V::n;
+  constexpr int QW = (NWS + V::n - 1) / V::n;
   const int k1 = a.k1[e], k2 = a.k2[e];
   T u1[NP], u2[NP];
 #pragma unroll
@@ -304,32 +305,37 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
       }
     }
   }
-  // difference form of the stored operator: (u_0, u_1 - u_0, ..., u_{2Np-1} - u_0)
-  {
-    const T ub = u1[0];
+  // difference form of the stored operator: each row holds the coefficients of
+  // (u1_1 - u_0, ..., u1_{Np-1} - u_0, u2_0 - u_0, ..., u2_{Np-1} - u_0), u_0 = u1_0, and the
+  // edge's last value s = J_f (v.n1) multiplies u_0 in every row
+  const T ub = u1[0];
 #pragma unroll
-    for (int j = 1; j < NP; ++j) u1[j] -= ub;
+  for (int j = 1; j < NP; ++j) u1[j] -= ub;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) u2[j] -= ub;
-  }
+  for (int j = 0; j < NP; ++j) u2[j] -= ub;
   const VT* w = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
   const bool keep = (e >> 5) < a.keep_tiles;
   const uint64_t pol = keep ? l2_keep_policy() : 0;
   T acc[NFP];
 #pragma unroll
   for (int r = 0; r < NFP; ++r) acc[r] = T(0);
+  T srow = T(0);
 #pragma unroll
   for (int q = 0; q < QW; ++q) {
     const VT v = keep ? ld_keep(w + q * kTile, pol) : ld_stream(w + q * kTile);
 #pragma unroll
     for (int cc = 0; cc < V::n; ++cc) {
       const int idx = q * V::n + cc;
-      if (idx < NW) {
-        const int r = idx / (2 * NP), j = idx % (2 * NP);
-        acc[r] = fma(V::get(v, cc), j < NP ? u1[j] : u2[j - NP], acc[r]);
+      if (idx < NWS - 1) {
+        const int r = idx / RW, j = idx % RW;
+        acc[r] = fma(V::get(v, cc), j < NP - 1 ? u1[j + 1] : u2[j - (NP - 1)], acc[r]);
+      } else if (idx == NWS - 1) {
+        srow = V::get(v, cc);
       }
     }
   }
+#pragma unroll
+  for (int r = 0; r < NFP; ++r) acc[r] = fma(srow, ub, acc[r]);
   if constexpr (FB) {
     // scatter to the two elements' face slots: side 1 in its face order, side 2 (outward
     // normal -n1, face traversed the other way) negated and reversed

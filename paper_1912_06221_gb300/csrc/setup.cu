@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   const int ff[2] = {f1, f2};
   const int64_t tile = e >> 5, le = e & 31;
   const int VW = 16 / elem_bytes;
-  const int QW = (NW + VW - 1) / VW;
+  const int QW = (NFP * (2 * NP - 1) + 1 + VW - 1) / VW;   // 16-byte words of the stored operator
 
   if (Pt) {
     // GEMM-form parameter record (FP32): psi_m(alpha_k, beta_k) of both sides, kappa_R,
@@ -298,14 +298,22 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
       if (side == 0 && vn >= 0 && col == (int)fmask[f1 * NFP + i]) w += Jf * vn;
       if (side == 1 && vn < 0 && col == (int)fmask[f2 * NFP + (NFP - 1 - i)]) w += Jf * vn;
       const int idx = i * 2 * NP + side * NP + col;
-      const int64_t off = ((tile * QW + idx / VW) * kTile + le) * VW + (idx % VW);
       // Stored (difference) form: the flux kernels apply the operator to
-      // (u_0, u_1 - u_0, ..., u_{2Np-1} - u_0), u_0 = side 1's first node value, so the
-      // stored column 0 is the row sum of W.  The reconstruction reproduces constants and
-      // their gradient vanishes, so the row sum is the upwind part alone, J_f (v.n1), and
-      // the large diffusive entries only ever multiply differences of nearby values.
-      const double wt = (side == 0 && col == 0) ? Jf * vn : w;
-      if (Wt) {
+      // (u_0, u_1 - u_0, ..., u_{2Np-1} - u_0), u_0 = side 1's first node value, so column 0
+      // would hold the row sum of W.  The reconstruction reproduces constants and their
+      // gradient vanishes, so that row sum is the upwind part alone, J_f (v.n1), the same for
+      // every row: it is stored once, after the rows' other 2 Np - 1 columns, and the large
+      // diffusive entries only ever multiply differences of nearby values.
+      constexpr int RW = 2 * NP - 1;
+      int sidx = -1;
+      if (side == 0 && col == 0) {
+        if (i == 0) sidx = NFP * RW;                           // the shared row sum
+      } else {
+        sidx = i * RW + (side == 0 ? col - 1 : NP - 1 + col);
+      }
+      if (Wt && sidx >= 0) {
+        const double wt = sidx == NFP * RW ? Jf * vn : w;
+        const int64_t off = ((tile * QW + sidx / VW) * kTile + le) * VW + (sidx % VW);
         if (elem_bytes == 4) static_cast<float*>(Wt)[off] = (float)wt;
         else static_cast<double*>(Wt)[off] = wt;
       }

@@ -46,7 +46,7 @@ def test_host_only_entry_points(lib):
     # admission bytes: W operator + indices + coefficients + fluxes + state buffers
     N, K, E = 4, 131072, 196608
     b = rdg.query_bytes(N, K, E, 0, rdg.FP32)
-    W = ((E + 31) // 32) * 38 * 32 * 16
+    W = ((E + 31) // 32) * 37 * 32 * 16          # ceil((5 * 29 + 1) / 4) = 37 words per edge
     assert b == W + 12 * E + 12 * K + 3 * K * 5 * 4 + 24 * K + E * 5 * 4 + 4 * K * 15 * 4
     assert rdg.query_bytes(N, K, E, 0, rdg.FP64) > b
     with pytest.raises(rdg.RdgError):
