@@ -216,3 +216,26 @@ def test_autotune_picks_a_valid_form_and_caches():
     assert c2["cached"] and c2["precision"] == c1["precision"]
     c6 = autotune.choose_precision(xy, tri, 6, D)
     assert c6["precision"] == rdg.FP32 and set(c6["ms"]) == {"fp32"}
+
+
+def test_batch_member_with_lsrk_integrator_equals_alone():
+    """A member stepped with the paper's low-storage scheme inside a batch (beside an
+    SSP-RK3 member) ends where the same solve alone does."""
+    specs = [(4, 6, rdg.FP32, PERIODIC, (0.4, 0.2), False), (2, 5, rdg.FP64, PERIODIC, (0.0, 0.0), False)]
+    items = _build(specs)
+    (_, a0, b0), (_, a1, b1) = items
+    a0[0].set_integrator(rdg.LSRK54)
+    b0[0].set_integrator(rdg.LSRK54)
+    bt = rdg.Batch(chunk=8)
+    bt.add(a0[0], a0[2])
+    bt.add(a1[0], a1[2])
+    bt.step(19)
+    bt.synchronize()
+    b0[0].solve_to_time(0.0, a0[2], 19)
+    b1[0].solve_to_time(0.0, a1[2], 19)
+    assert np.array_equal(a0[0].get_state_host(), b0[0].get_state_host())
+    assert np.array_equal(a1[0].get_state_host(), b1[0].get_state_host())
+    bt.close()
+    for (_, a, b) in items:
+        a[0].close()
+        b[0].close()
