@@ -251,11 +251,11 @@ __device__ __forceinline__ bool gemm_edge_tile(const EdgeArgs<float>& a, int64_t
     }
     mma_commit(bar);
   }
-  bool ok = mbar_wait(bar, phase, 1000000000ull);
-  if (!ok) {
-    dev::report(a.err, kErrWaitTimeout);
-    mbar_wait(bar, phase, 1000000000ull);   // give the tensor core a second chance to drain
-  }
+  const bool done = mbar_wait(bar, phase, 1000000000ull);
+  if (!done) mbar_wait(bar, phase, 1000000000ull);   // give the tensor core a second chance to drain
+  // the block agrees on the outcome, so every thread leaves the tile loop together
+  const bool ok = __syncthreads_and(done ? 1 : 0) != 0;
+  if (!ok && tid == 0) dev::report(a.err, kErrWaitTimeout);
   phase ^= 1u;
   tc_fence_after();
   // epilogue: acc_i = sum_side sum_m psi_m(side) D_side[(m, i)]

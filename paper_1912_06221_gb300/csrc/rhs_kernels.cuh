@@ -371,7 +371,8 @@ constexpr int stage_min_blocks() {
 
 // Operator stream kinds: 0 edge blocks only, fluxes to the per-edge buffer (allocation-free
 // entry point); 1 the fused form (edge and volume blocks interleaved, fluxes to the face
-// slots).
+// slots); 2 edge blocks only, fluxes to the face slots (the volume term from its own
+// kernel).
 template <typename T, int N, int KIND>
 __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_flux_kernel(EdgeArgs<T> a) {
   constexpr int NP = np_of(N);
@@ -633,6 +634,14 @@ inline int launch_edge_t(const EdgeArgs<T>& a, cudaStream_t s) {
   if constexpr (VOL) return launch_pdl(dev::edge_flux_kernel<T, N, 1>, (unsigned)(ge + gv), kStageBlock, s, a);
   dev::edge_flux_kernel<T, N, 0><<<(unsigned)ge, kStageBlock, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
+}
+
+// Edge blocks only, fluxes to the face slots, programmatic launch.
+template <typename T, int N>
+inline int launch_edge_fb_t(const EdgeArgs<T>& a, cudaStream_t s) {
+  if (a.E == 0) return RDG_OK;
+  const int64_t ge = (a.E + kStageBlock - 1) / kStageBlock;
+  return launch_pdl(dev::edge_flux_kernel<T, N, 2>, (unsigned)ge, kStageBlock, s, a);
 }
 
 template <typename T, int N, bool VOLIN = false>

@@ -42,6 +42,19 @@ __device__ int g_gtab[3 * kNp + kN + 1];
 }  // namespace
 #endif
 
+// The FP32 object of order 6 forms the volume term as a tensor-core GEMM (volume_gemm.cuh).
+#define RDG_VGEMM (RDG_TAG_IS_F && RDG_ORDER == 6)
+#if RDG_VGEMM
+#include <cstring>
+
+#include "gemm_kernels.cuh"
+#include "volume_gemm.cuh"
+namespace {
+using VS = rdg::gemm::VolShape<kN>;
+__device__ __align__(16) float4 g_vb[2 * VS::BTILE / 16];
+}  // namespace
+#endif
+
 namespace rdg {
 
 int RDG_CAT(upload_tab_, RDG_CAT(RDG_TAG, RDG_ORDER))() {
@@ -70,6 +83,15 @@ int RDG_CAT(upload_tab_, RDG_CAT(RDG_TAG, RDG_ORDER))() {
   if (cudaMemcpyToSymbol(g_xb, xb.data(), sizeof(g_xb)) != cudaSuccess) return RDG_ECUDA;
   if (cudaMemcpyToSymbol(g_gtab, gt.data(), sizeof(g_gtab)) != cudaSuccess) return RDG_ECUDA;
 #endif
+#if RDG_VGEMM
+  {
+    const RefOps* o = get_refops(kN, nullptr);
+    if (!o) return RDG_EINVAL;
+    std::vector<float> vb = gemm::pack_volume_operand<kN>(*o);
+    if (vb.size() * 4 != sizeof(g_vb)) return RDG_EINVAL;
+    if (cudaMemcpyToSymbol(g_vb, vb.data(), sizeof(g_vb)) != cudaSuccess) return RDG_ECUDA;
+  }
+#endif
   return RDG_OK;
 }
 
@@ -92,7 +114,16 @@ int RDG_CAT(launch_elem_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<
 }
 
 int RDG_CAT(launch_edge_vol_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_REAL>& a, cudaStream_t s) {
+#if RDG_VGEMM
+  // volume term on the tensor cores, then the edge blocks alone
+  void* vb = nullptr;
+  if (cudaGetSymbolAddress(&vb, g_vb) != cudaSuccess) return RDG_ECUDA;
+  const int rc = gemm::launch_volume_gemm_t<kN>(a, static_cast<const float4*>(vb), s);
+  if (rc != RDG_OK) return rc;
+  return launch_edge_fb_t<RDG_REAL, kN>(a, s);
+#else
   return launch_edge_t<RDG_REAL, kN, true>(a, s);
+#endif
 }
 
 int RDG_CAT(launch_elem_lite_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<RDG_REAL>& a, cudaStream_t s) {

@@ -32,6 +32,9 @@ def test_serve_mix_equals_alone_and_budget():
     __graft_entry__.build()
     from paper_1912_06221_gb300.serve import Server, request_bytes, solve_alone, latency_stats
     reqs = _requests()
+    # the first request runs long enough (tens of ms) that the next arrivals finish their
+    # set-up while it is resident, whatever the box's set-up speed relative to its solves
+    reqs[0].steps = 4000
     sizes = [request_bytes(r) for r in reqs]
     budget = sum(sorted(sizes)[-3:])          # at most ~3 resident at once: forces queueing
     srv = Server(budget_bytes=budget, max_slots=4, chunk=8)
