@@ -215,6 +215,9 @@ int rdg_destroy(rdg_ctx* ctx) {
   dfree(ctx->d_err, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return RDG_OK;
@@ -707,6 +710,26 @@ int64_t keep_tiles(const rdg_ctx* ctx) {
   return tile > 0 ? bytes / tile : 0;
 }
 
+// Volume kernel on a stream forked from `st` and joined back after the edge kernel, so the
+// tensor-core volume term and the HBM-bound operator stream share the SMs.  Works the same
+// eagerly and under graph capture (the fork and join become graph edges).
+int enqueue_split_stage(rdg_ctx* ctx, const EdgeArgs<float>& ea, cudaStream_t st) {
+  if (!ctx->side_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) return RDG_ECUDA;
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return RDG_ECUDA;
+    if (cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) return RDG_ECUDA;
+  }
+  if (cudaEventRecord(ctx->ev_fork, st) != cudaSuccess) return RDG_ECUDA;
+  if (cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0) != cudaSuccess) return RDG_ECUDA;
+  int rc = launch_volume32(ctx->N, ea, ctx->side_stream);
+  // the join is recorded even after a failed launch, so a capture never ends with the side
+  // stream still attached
+  if (cudaEventRecord(ctx->ev_join, ctx->side_stream) != cudaSuccess && rc == RDG_OK) rc = RDG_ECUDA;
+  if (rc == RDG_OK) rc = launch_edge_fb32(ctx->N, ea, st);
+  if (cudaStreamWaitEvent(st, ctx->ev_join, 0) != cudaSuccess && rc == RDG_OK) rc = RDG_ECUDA;
+  return rc;
+}
+
 template <typename T>
 int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta,
                   void* out2 = nullptr, T rka = T(0), T rkb = T(0)) {
@@ -723,8 +746,13 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
     for (auto& e : ev) e = take_event(ctx);
   int rc;
   if (prof) cudaEventRecord(ev[0], st);
-  if constexpr (sizeof(T) == 4) rc = ctx->gemm ? launch_gemm32(ctx->N, ea, st) : launch_edge_vol32(ctx->N, ea, st);
-  else rc = launch_edge_vol64(ctx->N, ea, st);
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->gemm) rc = launch_gemm32(ctx->N, ea, st);
+    else if (split_volume32(ctx->N)) rc = enqueue_split_stage(ctx, ea, st);
+    else rc = launch_edge_vol32(ctx->N, ea, st);
+  } else {
+    rc = launch_edge_vol64(ctx->N, ea, st);
+  }
   if (prof) {
     cudaEventRecord(ev[1], st);
     cudaEventRecord(ev[2], st);

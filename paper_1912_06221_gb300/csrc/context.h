@@ -21,6 +21,9 @@ struct rdg_ctx {
   cudaStream_t cap_stream = nullptr; // private stream used only to capture graphs
   bool capturing = false;
   bool own_stream = false;
+  // forked stream for a volume kernel that runs beside the edge kernel (FP32, order 6)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   // mesh (host)
   bool mesh_ok = false;

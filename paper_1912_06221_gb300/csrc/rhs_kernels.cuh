@@ -364,8 +364,12 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
 // Resident stage blocks per SM asked of the compiler (FP32: 5 blocks up to N = 4, <= 102
 // registers; 6 above, where more warps in flight measured faster than more registers per
 // thread; FP64: 4 up to N = 3, 3 above), so the operator stream keeps enough loads in flight.
-template <typename T, int N>
+// The edge-only form (kind 2) runs beside the order-6 volume kernel with fewer, larger blocks:
+// registers that would hold the volume role's values keep more operator loads in flight.
+constexpr int kEdgeOnlyBlocks = 3;
+template <typename T, int N, int KIND = 1>
 constexpr int stage_min_blocks() {
+  if (KIND == 2 && sizeof(T) == 4) return kEdgeOnlyBlocks;
   return sizeof(T) == 4 ? (N <= 4 ? 5 : 6) : (N <= 3 ? 4 : 3);
 }
 
@@ -374,7 +378,7 @@ constexpr int stage_min_blocks() {
 // slots); 2 edge blocks only, fluxes to the face slots (the volume term from its own
 // kernel).
 template <typename T, int N, int KIND>
-__global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N>()) edge_flux_kernel(EdgeArgs<T> a) {
+__global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N, KIND>()) edge_flux_kernel(EdgeArgs<T> a) {
   constexpr int NP = np_of(N);
   wait_for_predecessor();
   int64_t eblk = blockIdx.x;

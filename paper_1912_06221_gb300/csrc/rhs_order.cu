@@ -51,7 +51,7 @@ __device__ int g_gtab[3 * kNp + kN + 1];
 #include "volume_gemm.cuh"
 namespace {
 using VS = rdg::gemm::VolShape<kN>;
-__device__ __align__(16) float4 g_vb[2 * VS::BTILE / 16];
+__device__ __align__(16) float4 g_vb[VS::BWORDS];
 }  // namespace
 #endif
 
@@ -114,17 +114,21 @@ int RDG_CAT(launch_elem_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<
 }
 
 int RDG_CAT(launch_edge_vol_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_REAL>& a, cudaStream_t s) {
+  return launch_edge_t<RDG_REAL, kN, true>(a, s);
+}
+
 #if RDG_VGEMM
-  // volume term on the tensor cores, then the edge blocks alone
+// the volume term on the tensor cores, and the edge blocks alone (the stage launches them on
+// two streams so they overlap)
+int RDG_CAT(launch_volume_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<float>& a, cudaStream_t s) {
   void* vb = nullptr;
   if (cudaGetSymbolAddress(&vb, g_vb) != cudaSuccess) return RDG_ECUDA;
-  const int rc = gemm::launch_volume_gemm_t<kN>(a, static_cast<const float4*>(vb), s);
-  if (rc != RDG_OK) return rc;
-  return launch_edge_fb_t<RDG_REAL, kN>(a, s);
-#else
-  return launch_edge_t<RDG_REAL, kN, true>(a, s);
-#endif
+  return gemm::launch_volume_gemm_t<kN>(a, static_cast<const float4*>(vb), s);
 }
+int RDG_CAT(launch_edge_fb_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<float>& a, cudaStream_t s) {
+  return launch_edge_fb_t<float, kN>(a, s);
+}
+#endif
 
 int RDG_CAT(launch_elem_lite_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const ElemArgs<RDG_REAL>& a, cudaStream_t s) {
   return launch_elem_t<RDG_REAL, kN, true>(mode, a, s);

@@ -35,7 +35,8 @@ MEMBERS = [(1, 11, rdg.FP32, PERIODIC, (0.0, 0.0), False),
            (3, 9, rdg.FP32, DIRICHLET, (0.0, 0.0), True),
            (4, 6, rdg.FP64, PERIODIC, (-0.3, 0.8), False),
            (5, 13, rdg.FP32, PERIODIC, (1.0, 0.5), False),
-           (6, 5, rdg.FP64, DIRICHLET, (0.2, 0.0), True)]
+           (6, 5, rdg.FP64, DIRICHLET, (0.2, 0.0), True),
+           (6, 7, rdg.FP32, PERIODIC, (0.4, -0.2), False)]
 
 
 def _member(i, N, m, prec, bc, v, forced):
