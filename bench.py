@@ -61,6 +61,9 @@ def parse():
                    help="the paper's Gaussian diffusion / advection-diffusion convergence series instead")
     p.add_argument("--sweep", action="store_true", help="the N=3 manufactured-solution precision sweep instead")
     p.add_argument("--batch-chunk", type=int, default=25)
+    p.add_argument("--orders", action="store_true",
+                   help="the circle pulse stage at every order N = 1..6, FP32 and FP64, instead")
+    p.add_argument("--orders-list", default="1,2,3,4,5,6")
     return p.parse_args()
 
 
@@ -729,6 +732,65 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_orders(args):
+    """Graph-replayed SSP-RK3 stage of the circle pulse workload (m x m x 2 triangles) at each
+    order, FP32 and FP64: microseconds per stage, GDOF/s and the stage's algorithmic HBM
+    bytes (stored operators, element rows, face fluxes) per second."""
+    import torch
+    import paper_1912_06221_gb300 as rdg
+    from synth import circle_pulse
+    orders = [int(x) for x in args.orders_list.split(",") if x]
+    rows = []
+    clk = ClockSampler(0)
+    clk.start()
+    for N in orders:
+        w = circle_pulse(m=args.m, N=N)
+        for prec, esz, name in ((rdg.FP32, 4, "fp32"), (rdg.FP64, 8, "fp64")):
+            s = rdg.Solver(w.xy, w.tri, N, w.D_elem, v=w.v, precision=prec)
+            u = torch.zeros((s.K, s.Np), dtype=s.dtype, device="cuda")
+            s.set_state(u)
+            dt = 1e-9
+            per = 32 * 3                          # stages per timed replay (32 steps)
+            for _ in range(max(args.warmup, 1)):
+                s.solve_to_time(0.0, dt, 32)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(max(args.steps, 1)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s.stream)
+                s.solve_to_time(0.0, dt, 32)
+                b.record(s.stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b) * 1e3 / per)
+            us = float(np.median(ts))
+            E, K, Np, Nfp = s.E, s.K, s.Np, N + 1
+            w_bytes = E * (Nfp * (2 * Np - 1) + 1) * esz
+            # the headline's accounting at this order and precision: edge pass (operators, edge
+            # ids, face fluxes, stage input, volume term, element coefficients) and element pass
+            # (volume term, stage input, step start in two of three stages, output, ids, 1/J,
+            # face fluxes)
+            alg = (E * ((Nfp * (2 * Np - 1) + 1) * esz + 8 + Nfp * esz) + 2 * K * Np * esz + K * 5 * esz
+                   + int(K * ((3 + 2.0 / 3.0) * Np * esz + 12 + esz) + E * Nfp * esz))
+            rows.append({"N": N, "precision": name, "stage_us": us, "gdofs": s.K * Np / (us * 1e-6) / 1e9,
+                         "operator_mb": w_bytes / 1e6, "alg_mb": alg / 1e6, "alg_gbs": alg / (us * 1e-6) / 1e9})
+            s.synchronize()
+            s.close()
+    clocks = clk.stop()
+    peak, src = measured_peaks()
+    for r in rows:
+        r["frac_of_%s_hbm" % src] = r["alg_gbs"] / peak
+    line = {"metric": "stage time per order", "value": None, "unit": "us", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "circle_pulse %dx%dx2=%d jittered periodic triangles (seed 1), v=(1,0.5), "
+                                   "D=1 in r<0.25 else 1e-4, zero state, 32 SSP-RK3 steps per timed graph replay"
+                                   % (args.m, args.m, 2 * args.m * args.m),
+                       "l2_flush": "none: operators above 129 MB (FP32 N >= 5, FP64 N >= 4) stream from HBM; "
+                                   "smaller orders partly hit L2 across replays"},
+            "orders": rows, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -741,5 +803,7 @@ if __name__ == "__main__":
         run_paper_problems(a)
     elif a.sweep:
         run_sweep(a)
+    elif a.orders:
+        run_orders(a)
     else:
         run_ours(a)

@@ -19,6 +19,9 @@
 namespace rdg {
 namespace gemm {
 
+// Persistent volume blocks per SM at most (shared and tensor memory allow two at order 6).
+constexpr int kVolumeBlocksPerSm = 2;
+
 template <int N>
 struct VolShape {
   static constexpr int NP = np_of(N);
@@ -43,6 +46,7 @@ struct VolShape {
   static constexpr int SMEM = DATA > FLOOR ? DATA : FLOOR;
   static constexpr int RV = NP * 4 / 16;                  // 16-byte words of an element row
   static_assert(NPAD1 <= 256 && NPAD2 <= 256, "MMA N limit");
+  static_assert(NPAD1 % 32 == 0 && NPAD2 % 32 == 0, "epilogue reads 32 columns at a time");
   static_assert(NP * 4 % 16 == 0, "element rows of whole 16-byte words");
   static_assert(SMEM <= 232448, "shared memory per block");
 };
@@ -66,6 +70,23 @@ constexpr int max_tmem_cols(int i, int smem_left) {
   return best;
 }
 static_assert(max_tmem_cols(0, 233472) <= 512, "co-resident tcgen05 blocks could oversubscribe tensor memory");
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane (warp w reads lanes
+// 32w..32w+31), one completion wait per 32 columns.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
 
 // Persistent: B (hi, lo) copied into shared memory once, tensor-memory columns taken once
 // after the dependency wait, then element tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Each
@@ -186,22 +207,22 @@ __global__ void __launch_bounds__(128, 1) volume_gemm_kernel(EdgeArgs<float> a, 
     for (int i = 0; i < NP; ++i) vol[i] = 0.f;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-    for (int c = 0; c < S::NPAD1 / 16; ++c) {
-      float v[16];
-      tmem_ld16(lane_base + c * 16, v);
+    for (int c = 0; c < S::NPAD1 / 32; ++c) {
+      float v[32];
+      tmem_ld32(lane_base + c * 32, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = c * 16 + j;
+      for (int j = 0; j < 32; ++j) {
+        const int n = c * 32 + j;
         if (n < S::N1) vol[n % NP] = fmaf(co[n / NP], v[j], vol[n % NP]);
       }
     }
 #pragma unroll
-    for (int c = 0; c < S::NPAD2 / 16; ++c) {
-      float v[16];
-      tmem_ld16(lane_base + S::NPAD1 + c * 16, v);
+    for (int c = 0; c < S::NPAD2 / 32; ++c) {
+      float v[32];
+      tmem_ld32(lane_base + S::NPAD1 + c * 32, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = c * 16 + j;
+      for (int j = 0; j < 32; ++j) {
+        const int n = c * 32 + j;
         if (n < S::N2) vol[n % NP] = fmaf(co[2 + n / NP], v[j], vol[n % NP]);
       }
     }
@@ -277,7 +298,7 @@ int launch_volume_gemm_t(const EdgeArgs<float>& a, const float4* vb, cudaStream_
   if (ntiles == 0) return RDG_OK;
   // one wave of persistent blocks: as many per SM as both shared memory (1 KB reserved per
   // block) and tensor memory allow
-  const int per_sm = std::max(1, std::min(S::CTAS, 233472 / (S::SMEM + 1024)));
+  const int per_sm = std::max(1, std::min({S::CTAS, 233472 / (S::SMEM + 1024), kVolumeBlocksPerSm}));
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * sm_count());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
