@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--orders", action="store_true",
                    help="the circle pulse stage at every order N = 1..6, FP32 and FP64, instead")
     p.add_argument("--orders-list", default="1,2,3,4,5,6")
+    p.add_argument("--orders-precisions", default="fp32,fp64")
     return p.parse_args()
 
 
@@ -746,6 +747,8 @@ def run_orders(args):
     for N in orders:
         w = circle_pulse(m=args.m, N=N)
         for prec, esz, name in ((rdg.FP32, 4, "fp32"), (rdg.FP64, 8, "fp64")):
+            if name not in args.orders_precisions.split(","):
+                continue
             s = rdg.Solver(w.xy, w.tri, N, w.D_elem, v=w.v, precision=prec)
             u = torch.zeros((s.K, s.Np), dtype=s.dtype, device="cuda")
             s.set_state(u)

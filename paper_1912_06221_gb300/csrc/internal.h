@@ -110,7 +110,7 @@ int upload_elem_tables(int device);
 constexpr int kMaxGemmN = 5;
 int launch_gemm32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 // Orders whose FP32 volume term is its own tensor-core kernel (volume_gemm.cuh), launched
-// beside the edge-only operator stream (kind 2) instead of the fused stage kernel.
+// beside the edge-only operator stream (kind 2) instead of the fused stage kernel (order 6).
 bool split_volume32(int N);
 int launch_volume32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 int launch_edge_fb32(int N, const EdgeArgs<float>& a, cudaStream_t s);

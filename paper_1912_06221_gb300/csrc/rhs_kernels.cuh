@@ -364,12 +364,14 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
 // Resident stage blocks per SM asked of the compiler (FP32: 5 blocks up to N = 4, <= 102
 // registers; 6 above, where more warps in flight measured faster than more registers per
 // thread; FP64: 4 up to N = 3, 3 above), so the operator stream keeps enough loads in flight.
-// The edge-only form (kind 2) runs beside the order-6 volume kernel with fewer, larger blocks:
-// registers that would hold the volume role's values keep more operator loads in flight.
-constexpr int kEdgeOnlyBlocks = 3;
+// The edge-only form (kind 2) runs beside the tensor-core volume kernel with fewer, larger
+// blocks: registers that would hold the volume role's values keep more operator loads in
+// flight (order 6 measured 85, 83, 86 us per stage at 2, 3, 4 blocks per SM; orders 4 and 5
+// in that form were fastest at 5 and 4).
+constexpr int kEdgeOnlyBlocks[7] = {0, 5, 5, 5, 5, 4, 3};
 template <typename T, int N, int KIND = 1>
 constexpr int stage_min_blocks() {
-  if (KIND == 2 && sizeof(T) == 4) return kEdgeOnlyBlocks;
+  if (KIND == 2 && sizeof(T) == 4) return kEdgeOnlyBlocks[N];
   return sizeof(T) == 4 ? (N <= 4 ? 5 : 6) : (N <= 3 ? 4 : 3);
 }
 

@@ -42,7 +42,8 @@ __device__ int g_gtab[3 * kNp + kN + 1];
 }  // namespace
 #endif
 
-// The FP32 object of order 6 forms the volume term as a tensor-core GEMM (volume_gemm.cuh).
+// The FP32 object of order 6 also holds the volume term as a tensor-core GEMM
+// (volume_gemm.cuh), which its stage launches beside the edge-only operator stream.
 #define RDG_VGEMM (RDG_TAG_IS_F && RDG_ORDER == 6)
 #if RDG_VGEMM
 #include <cstring>

@@ -1,4 +1,7 @@
-// Volume term as a tensor-core GEMM (tcgen05, split 3xTF32), for the largest order.
+// Volume term as a tensor-core GEMM (tcgen05, split 3xTF32).  Written for any order (rows
+// of whole 16-byte words load as vectors, others element by element); the library builds it
+// for FP32 order 6, where it is faster than the fused stage kernel's volume role (at orders
+// 4 and 5 the split form measured 45.6 and 73.2 us per stage against 31.0 and 58.6 fused).
 //
 // The volume term of element k is a fixed linear combination of five products of the
 // element's values with shared reference matrices (the metric-folded form of M^{-1} S^T . F,
@@ -19,7 +22,8 @@
 namespace rdg {
 namespace gemm {
 
-// Persistent volume blocks per SM at most (shared and tensor memory allow two at order 6).
+// Persistent volume blocks per SM at most (shared and tensor memory allow two at order 6;
+// at lower orders the edge-only blocks running beside them keep the rest of the SM).
 constexpr int kVolumeBlocksPerSm = 2;
 
 template <int N>
@@ -29,7 +33,7 @@ struct VolShape {
   static constexpr int KD = (NP - 1 + 7) / 8 * 8;         // d block of A
   static constexpr int KP = KU + KD;
   static constexpr int N1 = 2 * NP, N2 = 3 * NP;          // rows of B1, B2
-  static constexpr int NPAD1 = (N1 + 15) / 16 * 16, NPAD2 = (N2 + 15) / 16 * 16;
+  static constexpr int NPAD1 = (N1 + 31) / 32 * 32, NPAD2 = (N2 + 31) / 32 * 32;   // MMA N, epilogue reads
   static constexpr int M = 128;
   static constexpr int SBO_A = KP / 4 * 128;              // bytes between 8-row groups of A
   static constexpr int SBO_B1 = KU / 4 * 128, SBO_B2 = KD / 4 * 128;
@@ -42,26 +46,28 @@ struct VolShape {
   static constexpr int OFF_B = 2 * ATILE;                 // A hi, lo; then B
   static constexpr int OFF_BAR = OFF_B + 2 * (BT1 + BT2);
   static constexpr int DATA = OFF_BAR + 16;
-  static constexpr int FLOOR = 233472 / (CTAS + 1) - 1024 + 16;
+  // shared-memory floor that keeps tensor memory from being oversubscribed (checked below for
+  // every mix): a block of four or more per SM's worth of columns takes a 1/CTAS share
+  static constexpr int FLOOR = CTAS >= 4 ? 233472 / CTAS - 1024 : 233472 / (CTAS + 1) - 1024 + 16;
   static constexpr int SMEM = DATA > FLOOR ? DATA : FLOOR;
-  static constexpr int RV = NP * 4 / 16;                  // 16-byte words of an element row
+  static constexpr bool VEC = NP * 4 % 16 == 0;           // element rows of whole 16-byte words
   static_assert(NPAD1 <= 256 && NPAD2 <= 256, "MMA N limit");
   static_assert(NPAD1 % 32 == 0 && NPAD2 % 32 == 0, "epilogue reads 32 columns at a time");
-  static_assert(NP * 4 % 16 == 0, "element rows of whole 16-byte words");
   static_assert(SMEM <= 232448, "shared memory per block");
 };
 
 // Tensor-memory columns: every mix of blocks of the tcgen05 kernels (edge GEMM form of orders
-// 1..5, this volume kernel) that fits one SM's 228 KB of shared memory (1 KB reserved per
+// 1..5, this volume kernel at order 6) that fits one SM's 228 KB of shared memory (1 KB reserved per
 // block) holds at most the SM's 512 columns, so an allocation never waits for another block.
 struct TmemUser {
   int smem, cols;
 };
-constexpr TmemUser kTmemUsers[6] = {{Shape<1>::SMEM, Shape<1>::TCOLS}, {Shape<2>::SMEM, Shape<2>::TCOLS},
-                                    {Shape<3>::SMEM, Shape<3>::TCOLS}, {Shape<4>::SMEM, Shape<4>::TCOLS},
-                                    {Shape<5>::SMEM, Shape<5>::TCOLS}, {VolShape<6>::SMEM, VolShape<6>::TCOLS}};
+constexpr int kNumTmemUsers = 6;
+constexpr TmemUser kTmemUsers[kNumTmemUsers] = {
+    {Shape<1>::SMEM, Shape<1>::TCOLS}, {Shape<2>::SMEM, Shape<2>::TCOLS}, {Shape<3>::SMEM, Shape<3>::TCOLS},
+    {Shape<4>::SMEM, Shape<4>::TCOLS}, {Shape<5>::SMEM, Shape<5>::TCOLS}, {VolShape<6>::SMEM, VolShape<6>::TCOLS}};
 constexpr int max_tmem_cols(int i, int smem_left) {
-  if (i == 6) return 0;
+  if (i == kNumTmemUsers) return 0;
   int best = 0;
   for (int c = 0; c * (kTmemUsers[i].smem + 1024) <= smem_left; ++c) {
     const int v = c * kTmemUsers[i].cols + max_tmem_cols(i + 1, smem_left - c * (kTmemUsers[i].smem + 1024));
@@ -95,7 +101,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 template <int N>
 __global__ void __launch_bounds__(128, 1) volume_gemm_kernel(EdgeArgs<float> a, const float4* vb) {
   using S = VolShape<N>;
-  constexpr int NP = S::NP, RV = S::RV;
+  constexpr int NP = S::NP;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   {
@@ -114,17 +120,28 @@ __global__ void __launch_bounds__(128, 1) volume_gemm_kernel(EdgeArgs<float> a, 
   const uint32_t tmem = *slot;
   const int64_t ntiles = (a.K + S::M - 1) / S::M;
   uint32_t phase = 0;
-  float4 nxt[RV];
+  float nxt[NP];
   int64_t t = blockIdx.x;
   auto load_row = [&](int64_t tt) {
     const int64_t kk = tt * S::M + tid;
     if (tt < ntiles && kk < a.K) {
-      const float4* p = reinterpret_cast<const float4*>(a.u + kk * NP);
+      if constexpr (S::VEC) {
+        const float4* p = reinterpret_cast<const float4*>(a.u + kk * NP);
 #pragma unroll
-      for (int q = 0; q < RV; ++q) nxt[q] = __ldg(p + q);
+        for (int q = 0; q < NP / 4; ++q) {
+          const float4 w = __ldg(p + q);
+          nxt[4 * q] = w.x;
+          nxt[4 * q + 1] = w.y;
+          nxt[4 * q + 2] = w.z;
+          nxt[4 * q + 3] = w.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) nxt[j] = __ldg(a.u + kk * NP + j);
+      }
     } else {
 #pragma unroll
-      for (int q = 0; q < RV; ++q) nxt[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < NP; ++j) nxt[j] = 0.f;
     }
   };
   load_row(t);
@@ -137,12 +154,7 @@ __global__ void __launch_bounds__(128, 1) volume_gemm_kernel(EdgeArgs<float> a, 
 #pragma unroll
       for (int c = 0; c < S::KP; ++c) row[c] = 0.f;
 #pragma unroll
-      for (int q = 0; q < RV; ++q) {
-        row[4 * q + 0] = nxt[q].x;
-        row[4 * q + 1] = nxt[q].y;
-        row[4 * q + 2] = nxt[q].z;
-        row[4 * q + 3] = nxt[q].w;
-      }
+      for (int j = 0; j < NP; ++j) row[j] = nxt[j];
 #pragma unroll
       for (int j = 1; j < NP; ++j) row[S::KU + j - 1] = row[j] - row[0];
       uint8_t* hi = smem + (tid >> 3) * S::SBO_A + (tid & 7) * 16;
@@ -228,9 +240,14 @@ __global__ void __launch_bounds__(128, 1) volume_gemm_kernel(EdgeArgs<float> a, 
     }
     tc_fence_before();
     if (live) {
-      float4* o = reinterpret_cast<float4*>(a.vol + k * NP);
+      if constexpr (S::VEC) {
+        float4* o = reinterpret_cast<float4*>(a.vol + k * NP);
 #pragma unroll
-      for (int q = 0; q < RV; ++q) o[q] = make_float4(vol[4 * q], vol[4 * q + 1], vol[4 * q + 2], vol[4 * q + 3]);
+        for (int q = 0; q < NP / 4; ++q) o[q] = make_float4(vol[4 * q], vol[4 * q + 1], vol[4 * q + 2], vol[4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) a.vol[k * NP + i] = vol[i];
+      }
     }
     __syncthreads();   // operand tiles and tensor memory free for the next tile
   }
