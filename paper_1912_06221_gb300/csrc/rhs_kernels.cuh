@@ -75,6 +75,10 @@ __device__ __forceinline__ double2 ld_keep(const double2* p, uint64_t pol) {
 // start while its predecessor in the stream finishes; it must wait here before touching any
 // data the predecessor reads or writes (a no-op for an ordinary launch).
 __device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel in the stream launch once every block of this grid has executed it
+// (or exited); the next kernel still waits for this grid's completion and memory before it
+// reads anything this grid writes.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void report(int* err, int bit) {
   if (err) atomicOr(err, bit);
@@ -383,6 +387,8 @@ template <typename T, int N, int KIND>
 __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N, KIND>()) edge_flux_kernel(EdgeArgs<T> a) {
   constexpr int NP = np_of(N);
   wait_for_predecessor();
+  // the element kernel may start its independent loads on SMs that the last wave leaves idle
+  if constexpr (KIND != 0) allow_dependents();
   int64_t eblk = blockIdx.x;
   if constexpr (KIND == 1) {
     __shared__ __align__(16) T sh[kStageBlock * NP];
@@ -521,21 +527,27 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
   const int tid = threadIdx.x;
   const bool active = tid < nk;
   const int64_t k = k0 + tid;
-  wait_for_predecessor();
-
+  // The stage input and the step start are written by no kernel of this stage (they come from
+  // the previous stage's element kernel, which the edge kernel waited for before it let this
+  // grid launch), so they are staged before the dependency wait, overlapping the edge
+  // kernel's last wave.
   {
-    Staged<T, BLK, NP> gv, gs, gn;
-    Staged<T, BLK, NQ> gq;
-    gv.load(a.vol + k0 * NP, nk * NP);
-    gq.load(a.fb + k0 * NQ, nk * NQ);
+    Staged<T, BLK, NP> gs, gn;
     if (MODE >= 1) gs.load(a.us + k0 * NP, nk * NP);
     if (MODE == 2 || MODE == 3 || (MODE == 4 && a.rka != T(0))) gn.load(a.un + k0 * NP, nk * NP);
-    gv.store(shv, nk * NP);
-    gq.store(shq, nk * NQ);
     if (MODE >= 1) gs.store(shs, nk * NP);
     if (MODE == 2 || MODE == 3 || (MODE == 4 && a.rka != T(0))) gn.store(shn, nk * NP);
   }
   const T ij = active ? a.geo[5 * a.K + k] : T(0);
+  wait_for_predecessor();
+  {
+    Staged<T, BLK, NP> gv;
+    Staged<T, BLK, NQ> gq;
+    gv.load(a.vol + k0 * NP, nk * NP);
+    gq.load(a.fb + k0 * NQ, nk * NQ);
+    gv.store(shv, nk * NP);
+    gq.store(shq, nk * NQ);
+  }
   if (tid < a.frc.nsrc) tau_s[tid] = (T)tau_of(a.frc.kind[tid], a.frc.omega[tid], stage_time(a.time));
   __syncthreads();
 
