@@ -714,10 +714,18 @@ int64_t keep_tiles(const rdg_ctx* ctx) {
 // tensor-core volume term and the HBM-bound operator stream share the SMs.  Works the same
 // eagerly and under graph capture (the fork and join become graph edges).
 int enqueue_split_stage(rdg_ctx* ctx, const EdgeArgs<float>& ea, cudaStream_t st) {
-  if (!ctx->side_stream) {
-    if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) return RDG_ECUDA;
-    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return RDG_ECUDA;
-    if (cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) return RDG_ECUDA;
+  // created on first use; each one again on a later call if its creation failed
+  if (!ctx->side_stream && cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->side_stream = nullptr;
+    return RDG_ECUDA;
+  }
+  if (!ctx->ev_fork && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    ctx->ev_fork = nullptr;
+    return RDG_ECUDA;
+  }
+  if (!ctx->ev_join && cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    ctx->ev_join = nullptr;
+    return RDG_ECUDA;
   }
   if (cudaEventRecord(ctx->ev_fork, st) != cudaSuccess) return RDG_ECUDA;
   if (cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0) != cudaSuccess) return RDG_ECUDA;
