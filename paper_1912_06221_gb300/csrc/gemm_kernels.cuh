@@ -326,6 +326,8 @@ __global__ void __launch_bounds__(128, 1) edge_gemm_kernel(EdgeArgs<float> a, co
   // tensor memory is taken only after the predecessor grid has finished, so this block never
   // holds columns while it waits on another kernel
   dev::wait_for_predecessor();
+  // the element kernel's blocks may fill SMs as these persistent blocks finish
+  dev::allow_dependents();
   if (threadIdx.x < 32) tmem_alloc(smem_u32(slot), S::TCOLS);
   fence_async_smem();
   tc_fence_before();
