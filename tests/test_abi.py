@@ -77,3 +77,22 @@ def test_create_without_gpu_fails_cleanly(lib):
     ctx = ctypes.c_void_p()
     rc = lib.rdg_create(ctypes.byref(ctx), 0, None)
     assert rc != 0 and lib.rdg_last_error(None)
+
+
+def test_missing_library_raises(tmp_path, monkeypatch):
+    """No CPU fallback: without the built library every entry raises."""
+    import paper_1912_06221_gb300.rdg as r
+    monkeypatch.setattr(r, "_lib", None)
+    with pytest.raises(RuntimeError):
+        r.load(str(tmp_path / "librdg.so"))
+
+
+def test_solver_without_gpu_raises(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    import paper_1912_06221_gb300 as rdg
+    from synth import unit_square_mesh
+    xy, tri = unit_square_mesh(4, 0.1, 1)
+    with pytest.raises(Exception):
+        rdg.Solver(xy, tri, 2, 1.0)
