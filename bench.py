@@ -37,7 +37,6 @@ METRIC = "recDG diffusion RHS GDOF/s, FP32 vs FP64 at stated L2 err; serve p50/p
 UNIT = "GDOF/s"
 N_ORDER = 4
 RK_STEPS = 500
-ORACLE_SAMPLE_M = 64
 
 
 def parse():
@@ -137,17 +136,44 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def profiled_traffic(args):
-    """DRAM bytes (read + write) per launch of the stage kernel from the committed ncu
-    summary of this workload, or None for another workload."""
-    if args.m != 256 or args.rk_steps <= 0:
-        return None
-    import re
-    p = os.path.join(ROOT, "profiles", "stage_kernels_circle_pulse_N4_m256_fp32.md")
-    if not os.path.exists(p):
-        return None
-    m = re.search(r"traffic_bytes_per_launch edge_flux_kernel<float,4,1>: (\d+)", open(p).read())
-    return int(m.group(1)) if m else None
+TRAFFIC_CSV = os.path.join(ROOT, "profiles", "stage_kernels_circle_pulse_N4_m256_fp32_dram.csv")
+STAGE_SOURCES = ("rhs_kernels.cuh", "rhs_order.cu", "internal.h")
+
+
+def stage_source_hash():
+    """sha256 (first 16 hex digits) of the stage kernels' sources, to tell whether a stored
+    ncu capture still describes the kernels being timed."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1912_06221_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(args, kernel="edge_flux_kernel<float, 4, 1>"):
+    """DRAM bytes (read + write) per launch of `kernel`, averaged over the launches of the
+    committed ncu capture of this workload (steady state: no cache flush between launches),
+    or None for another workload or when the kernels' sources changed after the capture
+    (the capture records the source hash on its first line)."""
+    if args.m != 256 or args.rk_steps <= 0 or args.precision != "fp32" or not os.path.exists(TRAFFIC_CSV):
+        return None, "no capture for this workload"
+    import csv
+    with open(TRAFFIC_CSV) as fh:
+        first = fh.readline()
+        if ("source_sha16=" + stage_source_hash()) not in first:
+            return None, "stage kernel sources changed since the capture"
+        rows = [r for r in csv.DictReader(line for line in fh if not line.startswith("=="))]
+    per = {}
+    for r in rows:
+        if r.get("Kernel Name", "").replace("void ", "").startswith(kernel):
+            if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                per.setdefault(r["ID"], 0.0)
+                per[r["ID"]] += float(r["Metric Value"].replace(",", ""))
+    if not per:
+        return None, "kernel not in the capture"
+    return float(np.mean(list(per.values()))), "%s (ncu, %d launches, no cache flush)" % (
+        os.path.relpath(TRAFFIC_CSV, ROOT), len(per))
 
 
 def measured_peaks():
@@ -158,30 +184,78 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def alg_bytes_per_element(N, esz):
+    """Algorithmic HBM bytes per element per right-hand-side stage of the stored-operator
+    form: read the stage input and step start and write the output (3 Np values), the Nfp x
+    2Np operator of 1.5 edges, and 56 bytes (FP32; 88 in FP64) of element coefficients and
+    edge/element ids.  Intermediates (face fluxes, volume term) are not counted."""
+    Np, Nfp = (N + 1) * (N + 2) // 2, N + 1
+    return esz * (3 * Np + 3 * Nfp * Np) + (56 if esz == 4 else 88)
+
+
 # ---------------------------------------------------------------------------------------
-def oracle_sample_gdofs(seconds_budget=12.0, m=ORACLE_SAMPLE_M):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the same
-    recipe on an m x m x 2 mesh, setup excluded, SSP-RK3 steps until the budget is used."""
-    from synth import circle_pulse
-    from oracle.mesh import Mesh
-    from oracle.rhs import Problem
-    w = circle_pulse(m=m, N=N_ORDER)
-    me = Mesh(w.xy, w.tri, w.N)
-    pr = Problem(me, w.D_elem, v=w.v)
-    u = w.u0(me.x, me.y)
-    dt = 1e-7
+# The oracle leg.  Only this leg (and --impl reference) runs the FP64 NumPy oracle: on
+# sampled elements of the full-size workload, through patches of their neighbourhoods
+# (oracle/patch.py), so the right-hand side and one SSP-RK3 step on those elements are the
+# oracle's exact values for the full 131072-triangle mesh.
+
+def oracle_sample(w, seed=0, n_random=512):
+    """Sampled elements: random ones, the first and the last (ragged) element tiles, elements
+    on the periodic boundary and on the D jump."""
+    K = w.K
+    rng = np.random.default_rng(seed)
+    from synth import centroids
+    c = centroids(w.xy, w.tri)
+    h = 1.0 / w.m
+    r = np.hypot(c[:, 0] - 0.5, c[:, 1] - 0.5)
+    on_jump = np.flatnonzero(np.abs(r - 0.25) < h)
+    on_edge = np.flatnonzero((c[:, 0] < h) | (c[:, 0] > 1 - h) | (c[:, 1] < h) | (c[:, 1] > 1 - h))
+    picks = [rng.choice(K, n_random, replace=False), np.arange(32), np.arange(K - 32, K),
+             rng.choice(on_jump, min(64, on_jump.size), replace=False),
+             rng.choice(on_edge, min(64, on_edge.size), replace=False)]
+    return np.unique(np.concatenate(picks))
+
+
+def oracle_leg(w, iface, rhs_sample, step_sample, u_rhs, t_rhs, u_step, dt, seconds_budget=10.0):
+    """Oracle values on the sampled elements (right-hand side of u_rhs at t_rhs; one SSP-RK3
+    step of u_step from t = 0 with dt) and the oracle's own throughput on the right-hand-side
+    patch, timed on the host cores (setup excluded)."""
+    from oracle.patch import PatchProblem, face_neighbours
+    nbr = face_neighbours(w.xy, w.tri)
     t0 = time.perf_counter()
+    p1 = PatchProblem(w.xy, w.tri, w.N, w.D_elem, rhs_sample, v=w.v, rings=1, interface=iface, nbr=nbr)
+    p3 = PatchProblem(w.xy, w.tri, w.N, w.D_elem, step_sample, v=w.v, rings=3, interface=iface, nbr=nbr)
+    t_setup = time.perf_counter() - t0
+    rhs = {k: p1.rhs(u, t_rhs) for k, u in u_rhs.items()}
+    step = {k: p3.rk3_step(u, 0.0, dt) for k, u in u_step.items()}
+    u0 = next(iter(u_rhs.values()))
     n = 0
+    t0 = time.perf_counter()
     while True:
-        u = pr.rk3_step(u, n * dt, dt)
+        p1.rhs(u0, t_rhs)
         n += 1
         el = time.perf_counter() - t0
-        if el > seconds_budget or n >= 400:
+        if el > seconds_budget or n >= 2000:
             break
-    gd = me.K * me.ops.Np * 3 * n / el / 1e9
-    return gd, {"kind": "oracle", "cores": 1, "sample": "FP64 NumPy oracle, same recipe on %dx%dx2 = %d triangles "
-                "(1/%d of the workload), %d SSP-RK3 steps = %d right-hand sides, %.1f s, setup excluded, "
-                "BLAS pinned to 1 thread" % (m, m, me.K, (256 // m) ** 2, n, 3 * n, el)}
+    Np = (w.N + 1) * (w.N + 2) // 2
+    gd = p1.patch_elements * Np * n / el / 1e9
+    meta = {"kind": "oracle", "cores": 1, "nproc": os.cpu_count(),
+            "blas_threads": os.environ.get("OMP_NUM_THREADS"),
+            "sample": "FP64 NumPy oracle (Algorithm %s) on a %d-element patch of the full %d-triangle mesh (the "
+                      "%d sampled elements and their face neighbours), %d right-hand sides in %.1f s, setup (%.1f s, "
+                      "both patches) excluded, BLAS pinned to 1 thread"
+                      % ("1" if iface == "alg1" else "2", p1.patch_elements, w.K, len(rhs_sample), n, el, t_setup)}
+    return gd, meta, rhs, step
+
+
+def compare_rows(got, want):
+    """Element-wise and normwise relative errors of sampled rows."""
+    got = np.asarray(got, float)
+    want = np.asarray(want, float)
+    d = got - want
+    return {"max_abs_over_max_ref": float(np.abs(d).max() / np.abs(want).max()),
+            "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(want)),
+            "elements": int(want.shape[0])}
 
 
 def run_reference(args):
@@ -189,39 +263,38 @@ def run_reference(args):
     if rank != 0:
         return
     from synth import circle_pulse
-    from oracle.mesh import Mesh
-    from oracle.rhs import Problem
-    w = circle_pulse(m=ORACLE_SAMPLE_M, N=N_ORDER)
-    me = Mesh(w.xy, w.tri, w.N)
-    pr = Problem(me, w.D_elem, v=w.v)
-    u = w.u0(me.x, me.y)
-    dt = 1e-7
-    per_step = 8           # RK steps of the sample in one bench step
+    from oracle.patch import PatchProblem
+    w = circle_pulse(m=args.m, N=N_ORDER)
+    sample = oracle_sample(w)
+    pp = PatchProblem(w.xy, w.tri, w.N, w.D_elem, sample, v=w.v, rings=1, interface="alg1")
+    u = w.u0(pp.mesh.x, pp.mesh.y)
+    per_step = 40          # right-hand sides of the patch in one bench step
     for i in range(args.warmup):
         for j in range(per_step):
-            u = pr.rk3_step(u, 0.0, dt)
+            pp.problem.rhs(u, 0.0)
     t0 = time.perf_counter()
     for i in range(args.steps):
         for j in range(per_step):
-            u = pr.rk3_step(u, 0.0, dt)
+            pp.problem.rhs(u, 0.0)
     el = time.perf_counter() - t0
-    val = me.K * me.ops.Np * 3 * per_step * args.steps / el / 1e9
+    val = pp.patch_elements * pp.mesh.ops.Np * per_step * args.steps / el / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": "FP64 NumPy oracle, same recipe on %dx%dx2 = %d triangles, %d SSP-RK3 "
-                                       "steps per bench step, setup excluded, BLAS pinned to 1 thread"
-                                       % (ORACLE_SAMPLE_M, ORACLE_SAMPLE_M, me.K, per_step)},
+            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": 1, "nproc": os.cpu_count(),
+                             "sample": "FP64 NumPy oracle (Algorithm 1) on a %d-element patch of the full %d-triangle "
+                                       "mesh (%d sampled elements and their face neighbours), %d right-hand sides "
+                                       "per bench step, setup excluded, BLAS pinned to 1 thread"
+                                       % (pp.patch_elements, w.K, len(sample), per_step)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def workload_config(args):
     return {"workload": "circle_pulse N=4 (Np=15), %dx%dx2=%d jittered periodic triangles (seed 1), v=(1,0.5), "
-                        "D=1 in r<0.25 else 1e-4, Gaussian w=0.05, %d SSP-RK3 steps at 0.5x stability bound"
-                        % (args.m, args.m, 2 * args.m * args.m, args.rk_steps),
+                        "D=1 in r<0.25 else 1e-4 (Algorithm 1 interface rule), Gaussian w=0.05, %d SSP-RK3 steps "
+                        "at 0.5x stability bound" % (args.m, args.m, 2 * args.m * args.m, args.rk_steps),
             "N": N_ORDER, "triangles": 2 * args.m * args.m, "rk_steps_per_bench_step": args.rk_steps,
             "rhs_per_bench_step": 3 * args.rk_steps,
             "precision": "fp32" if args.precision == "fp32" else "fp32 state, edge flux as split-3xTF32 tensor-core GEMM",
@@ -263,8 +336,12 @@ def run_ours(args):
     from synth import circle_pulse
     w = circle_pulse(m=args.m, N=N_ORDER)
     gemm = args.precision == "tf32"
+    # The paper's Algorithm 1 for the element-wise D: on this 1e4 jump Algorithm 2's operator
+    # has eigenvalues with positive real part and the solve grows without bound (reported
+    # below as a labelled extra); the kernels and bytes are the same for both rules.
+    iface = rdg.IFACE_HARMONIC if gemm else rdg.IFACE_ALG1
     s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32_3XTF32 if gemm else rdg.FP32,
-                   device=local)
+                   device=local, interface=iface)
     stream = torch.cuda.current_stream()
     xyn = s.node_coords()
     u0_host = w.u0(xyn[..., 0], xyn[..., 1]).astype(np.float32)
@@ -310,35 +387,49 @@ def run_ours(args):
     edge_n, edge_ms = st["edge"]
     elem_n, elem_ms = st["elem"]
     E, K, Np, Nfp = s.E, s.K, s.Np, s.Nfp
-    # fused edge kernel: operator stream, edge ids, flux write, stage input (read once),
-    # volume-term write, five element coefficients
-    # (stored operator: Nfp (2 Np - 1) + 1 values per edge, the row sum stored once)
+    # the survey's algorithmic bytes of one stage (stored operators, state in and out,
+    # coefficients and ids); the stage kernel is the dominant launch
+    stage_alg = alg_bytes_per_element(N_ORDER, 4) * K
+    # the two kernels' own bytes, intermediates (volume term, face fluxes) included
     edge_bytes = E * ((Nfp * (2 * Np - 1) + 1) * 4 + 8 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
     if gemm:   # parameter records (16-byte words) instead of operators, plus the face-pair word
         edge_bytes = E * (((2 * Np + Nfp + 3 + 3) // 4) * 16 + 12 + Nfp * 4) + K * Np * 4 + K * Np * 4 + K * 5 * 4
-    # surface/stage kernel, averaged over the three stages (the step start is read in two):
-    # volume term, stage input, step start, output, edge ids, 1/J, face fluxes
     elem_bytes = int(K * ((3 + 2.0 / 3.0) * Np * 4 + 12 + 4) + E * Nfp * 4)
     peak, peak_kind = measured_peaks()
     edge_avg = edge_ms / edge_n
     elem_avg = elem_ms / elem_n
-    ach = edge_bytes / (edge_avg / 1e3) / 1e9
+    ach = stage_alg / (edge_avg / 1e3) / 1e9
+    traffic, traffic_src = (None, "GEMM form: no capture") if gemm else profiled_traffic(args)
     roof = {"bound": "hbm", "kernel": "edge_gemm_kernel<4>" if gemm else "edge_flux_kernel<float,4,VOL=1>",
-            "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "peak_source": peak_kind, "traffic": None if gemm else profiled_traffic(args),
-            "traffic_source": "profiles/stage_kernels_circle_pulse_N4_m256_fp32.md (ncu, one launch)",
-            "alg_bytes_per_launch": edge_bytes, "avg_launch_us": edge_avg * 1e3,
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind, "traffic": traffic,
+            "traffic_source": traffic_src,
+            "alg_bytes_per_launch": stage_alg,
+            "alg_bytes_rule": "%d B per element per stage (stored operators, state in/out, coefficients, ids) x K"
+                              % alg_bytes_per_element(N_ORDER, 4),
+            "avg_launch_us": edge_avg * 1e3,
             "share_of_kernel_time": edge_ms / (edge_ms + elem_ms),
-            "elem_kernel": {"name": "elem_lite_kernel<float,4,MODE>", "alg_bytes_per_launch": elem_bytes,
-                            "avg_launch_us": elem_avg * 1e3,
-                            "achieved_gbs": elem_bytes / (elem_avg / 1e3) / 1e9},
-            "stage_roofline_frac": (edge_bytes + elem_bytes) / ((edge_avg + elem_avg) / 1e3) / 1e9 / peak}
-    # the whole stage inside the replayed graph (programmatic dependent launch, warm L2): the
-    # algorithmic bytes of both kernels over the timed solve's time per stage
+            "kernel_own_bytes": {"edge_flux_kernel": edge_bytes, "elem_lite_kernel": elem_bytes,
+                                 "note": "each kernel's own reads and writes, volume-term and face-flux round "
+                                         "trips included (most of them hit L2 in steady state)"},
+            "elem_kernel": {"name": "elem_lite_kernel<float,4,MODE>", "avg_launch_us": elem_avg * 1e3}}
+    # the whole stage inside the replayed graph (programmatic dependent launch): the same
+    # algorithmic bytes over the timed solve's time per stage
     t_stage_s = t_ms / args.steps / (3 * nrk) / 1e3
-    roof["whole_stage_in_graph"] = {"alg_bytes": edge_bytes + elem_bytes, "us": t_stage_s * 1e6,
-                                    "achieved_gbs": (edge_bytes + elem_bytes) / t_stage_s / 1e9,
-                                    "frac": (edge_bytes + elem_bytes) / t_stage_s / 1e9 / peak}
+    roof["whole_stage_in_graph"] = {"alg_bytes": stage_alg, "us": t_stage_s * 1e6,
+                                    "achieved_gbs": stage_alg / t_stage_s / 1e9,
+                                    "frac": stage_alg / t_stage_s / 1e9 / peak}
+
+    # the compute side: measured FMA rates (in-process, this GPU at its current clocks) and
+    # the survey's flops per element per stage, 8 Np^2 + 12 Np Nfp + 12 Np
+    p32, p64 = rdg.peak_fma(local, rdg.FP32), rdg.peak_fma(local, rdg.FP64)
+    flops_stage = (8 * Np * Np + 12 * Np * Nfp + 12 * Np) * K
+    roof["rhs_roofline"] = {"t_bytes_us": stage_alg / (peak * 1e9) * 1e6, "t_flops_us": flops_stage / p32 * 1e6,
+                            "bound": "hbm" if stage_alg / (peak * 1e9) >= flops_stage / p32 else "fp32",
+                            "frac": max(stage_alg / (peak * 1e9), flops_stage / p32) / t_stage_s,
+                            "flops_per_stage": flops_stage}
+    compute_peaks = {"fp32_tflops": p32 / 1e12, "fp64_tflops": p64 / 1e12,
+                     "how": "rdg_peak_fma: independent FMA chains on every SM, CUDA events, best of 4"}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_t = []
@@ -354,14 +445,15 @@ def run_ours(args):
     e2e_val = s.K * s.Np * 3 * nrk * world / (float(np.mean(e2e_t))) / 1e9
 
     fp64 = None
+    s64_head = None
     if not args.no_fp64:
-        # the same solve in FP64, for the paper's interface rule (Algorithm 2) and the
-        # harmonic one: FP32-vs-FP64 differences at t_final and the size of the solution
+        # the same solve in FP64 on the GPU for each interface rule: FP32-vs-FP64 differences
+        # at t_final and the size of the solution (Algorithm 2 grows on this jump)
         fp64 = {}
         u64s = {}
-        for rule, name in ((rdg.IFACE_ALG2, "algorithm2"), (rdg.IFACE_HARMONIC, "harmonic"),
-                           (rdg.IFACE_ALG1, "algorithm1")):
-            if rule == rdg.IFACE_ALG2:
+        rules = ((rdg.IFACE_ALG1, "algorithm1"), (rdg.IFACE_ALG2, "algorithm2"), (rdg.IFACE_HARMONIC, "harmonic"))
+        for rule, name in rules:
+            if rule == iface:
                 u32 = u_fp32
             else:
                 s32 = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32, device=local, interface=rule)
@@ -386,32 +478,41 @@ def run_ours(args):
             fp64[name] = {"fp64_value": s.K * s.Np * 3 * nrk / (t64 / 1e3) / 1e9, "unit": UNIT,
                           "fp32_rel_l2_vs_fp64": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
                           "fp32_rel_linf_vs_fp64": float(np.abs(u32 - u64).max() / np.abs(u64).max()),
-                          "max_abs_u_t_final": float(np.abs(u64).max()), "t_final": nrk * dt}
-            s64.close()
+                          "max_abs_u_t_final": float(np.abs(u64).max()), "t_final": nrk * dt,
+                          "roofline_fp64": {"t_bytes_us": alg_bytes_per_element(N_ORDER, 8) * K / (peak * 1e9) * 1e6,
+                                            "t_flops_us": flops_stage / p64 * 1e6,
+                                            "stage_us": t64 / 1e3 / (3 * nrk) * 1e6,
+                                            "frac": max(alg_bytes_per_element(N_ORDER, 8) * K / (peak * 1e9),
+                                                        flops_stage / p64) / (t64 / 1e3 / (3 * nrk))},
+                          "role": ("headline" if rule == iface else
+                                   "extra: grows without bound on this jump" if rule == rdg.IFACE_ALG2 else "extra")}
+            if name == "algorithm1":
+                s64_head = s64
+            else:
+                s64.close()
 
     # the same solve with the GEMM form of the edge flux (tcgen05, split 3xTF32)
     tf32 = None
     if fp64 and not gemm:
-        # harmonic interface rule: the same kernels and speed as Algorithm 2, but a stable
-        # operator, so the difference to FP64 is rounding and not amplified growth
-        st = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32_3XTF32, device=local,
-                        interface=rdg.IFACE_HARMONIC)
-        st.set_state(u0)
-        st.solve_to_time(0.0, dt, nrk)
+        # harmonic interface rule (the GEMM form folds a single edge coefficient)
+        st_ = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32_3XTF32, device=local,
+                         interface=rdg.IFACE_HARMONIC)
+        st_.set_state(u0)
+        st_.solve_to_time(0.0, dt, nrk)
         torch.cuda.synchronize()
         tt = []
         for _ in range(max(2, args.steps // 2)):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            st.set_state(u0)
-            st.solve_to_time(0.0, dt, nrk)
+            st_.set_state(u0)
+            st_.solve_to_time(0.0, dt, nrk)
             b.record(stream)
             torch.cuda.synchronize()
             tt.append(a.elapsed_time(b))
-        ut = st.get_state_host().astype(np.float64)
-        st.synchronize()
-        st.close()
+        ut = st_.get_state_host().astype(np.float64)
+        st_.synchronize()
+        st_.close()
         u64 = u64s["harmonic"]
         tf32 = {"value": s.K * s.Np * 3 * nrk / (float(np.median(tt)) / 1e3) / 1e9, "unit": UNIT,
                 "kernel": "edge_gemm_kernel<4> (tcgen05.mma kind::tf32, split 3xTF32) + elem_lite_kernel",
@@ -419,20 +520,57 @@ def run_ours(args):
                 "rel_linf_vs_fp64": float(np.abs(ut - u64).max() / np.abs(u64).max()),
                 "interface": "harmonic"}
 
+    # the oracle leg (rank 0 of a single-GPU run): the FP64 oracle on sampled elements of the
+    # full mesh, element by element against the GPU's right-hand side and one SSP-RK3 step,
+    # FP32 and FP64, and the oracle's own throughput as the CPU baseline
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gd, meta = oracle_sample_gdofs()
+    vs_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not gemm:
+        samp = oracle_sample(w)
+        samp3 = oracle_sample(w, seed=1, n_random=64)[::2]
+        ur = np.random.default_rng(5).standard_normal((s.K, s.Np))
+        ins = {"pulse": w.u0(xyn[..., 0], xyn[..., 1]), "random": ur}
+        gpu = {}
+        solvers = [("fp32", s, np.float32)] + ([("fp64", s64_head, np.float64)] if s64_head is not None else [])
+        for pname, sv, npt in solvers:
+            for iname, uin in ins.items():
+                ud = torch.tensor(uin.astype(npt), device="cuda")
+                rd = torch.empty_like(ud)
+                sv.rhs_eval(ud, rd, 0.0)
+                sv.synchronize()
+                gpu[(pname, "rhs", iname)] = rd.cpu().numpy()[samp]
+            sv.set_state(torch.tensor(ins["pulse"].astype(npt), device="cuda"))
+            sv.rk_step(0.0, dt)
+            gpu[(pname, "step", "pulse")] = sv.get_state_host()[samp3]
+        # the oracle sees the values the GPU saw (FP32 inputs rounded as the FP32 path reads them)
+        u_rhs = {iname: uin for iname, uin in ins.items()}
+        u_rhs32 = {iname: uin.astype(np.float32).astype(np.float64) for iname, uin in ins.items()}
+        gd, meta, o_rhs, o_step = oracle_leg(w, "alg1", samp, samp3, {**{k + "64": v for k, v in u_rhs.items()},
+                                                                       **{k + "32": v for k, v in u_rhs32.items()}},
+                                             0.0, {"pulse64": ins["pulse"],
+                                                   "pulse32": ins["pulse"].astype(np.float32).astype(np.float64)}, dt)
         cpu = dict(value=gd, unit=UNIT, **meta)
+        vs_oracle = {"interface": "algorithm1", "sampled_elements_rhs": int(len(samp)),
+                     "sampled_elements_step": int(len(samp3)),
+                     "tolerance": {"fp32": 1e-5, "fp64": 1e-12}}
+        for pname, _, _ in solvers:
+            tag = "32" if pname == "fp32" else "64"
+            vs_oracle[pname] = {
+                "rhs_pulse": compare_rows(gpu[(pname, "rhs", "pulse")], o_rhs["pulse" + tag]),
+                "rhs_random": compare_rows(gpu[(pname, "rhs", "random")], o_rhs["random" + tag]),
+                "rk3_step_pulse": compare_rows(gpu[(pname, "step", "pulse")], o_step["pulse" + tag])}
+    if s64_head is not None:
+        s64_head.close()
 
     per_solve = (1 + (nrk // 16) * (16 * 6 + 1) if nrk >= 16 else 0) + (nrk % 16) * 6
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args), "dt": dt, "rho": rho,
-            "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "fp32_vs_oracle_full_mesh": vs_oracle,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
                     "d2h_bytes_per_step": int(out_pinned.numel() * out_pinned.element_size())},
-            "gpu_launches": per_solve * args.steps,
+            "gpu_launches": per_solve * args.steps, "compute_peaks": compute_peaks,
             "fp64_gpu": fp64, "fp32_3xtf32": tf32}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -614,15 +752,13 @@ def run_paper_problems(args):
     8192 triangles, every triangle pair a parallelogram, periodic 10 x 10 square with the
     image-sum exact solution), FP64 on the GPU with the paper's five-stage fourth-order
     Runge-Kutta scheme at a time step fixed by the finest mesh.  Reports L2 / L_inf errors
-    (Eqs. L2_norm_cellUnit, Linf_norm_cellUnit), two-mesh orders, and the paper's Tables
+    (Eqs. L2_norm_cellUnit, Linf_norm_cellUnit, in FP64 on the GPU), two-mesh orders, and the paper's Tables
     purediff_ooa / adv_diff_ooa (grid a) beside them."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_1912_06221_gb300 as rdg
     from synth import paper_gaussian
-    from oracle.mesh import Mesh            # error norms only (quadrature against the exact solution)
-    from oracle.rhs import error_norms
     tables = {False: {1: 2.015, 2: 2.828, 3: 4.005}, True: {1: 1.690, 2: 2.629, 3: 3.970}}
     ms = (4, 8, 16, 32, 64)
     out = {}
@@ -642,10 +778,10 @@ def run_paper_problems(args):
                 xyn = s.node_coords()
                 s.set_state(w.exact(xyn[..., 0], xyn[..., 1], 0.0))
                 s.solve_to_time(0.0, dt, n)
-                u = s.get_state_host()
+                q = s.error_quadrature()
+                e2, ei = s.error_norms(w.exact(q[..., 0], q[..., 1], 0.5))     # FP64 on the GPU
                 s.synchronize()
                 s.close()
-                e2, ei = error_norms(Mesh(w.xy, w.tri, N, period=(10.0, 10.0)), u, w.exact, 0.5)
                 l2.append(e2)
                 li.append(ei)
             key = "%s_P%d" % ("advection_diffusion" if adv else "diffusion", N)
@@ -673,8 +809,6 @@ def run_sweep(args):
     __graft_entry__.build()
     import paper_1912_06221_gb300 as rdg
     from synth import manufactured_dirichlet
-    from oracle.mesh import Mesh            # error norms only
-    from oracle.rhs import error_norms
     modes = (("fp64", rdg.FP64), ("fp32", rdg.FP32), ("fp32_3xtf32", rdg.FP32_3XTF32))
     rows = []
     for m in (32, 64, 128, 256, 512, 1024):
@@ -713,7 +847,8 @@ def run_sweep(args):
             row[name + "_gdof_per_s"] = s.K * s.Np * 3 * row["steps"] / (ms_ / 1e3) / 1e9
             states[name] = u
             if full:
-                e2, ei = error_norms(Mesh(w.xy, w.tri, w.N, bc=rdg.BC_DIRICHLET), u, w.exact, row["dt"] * row["steps"])
+                q = s.error_quadrature()
+                e2, ei = s.error_norms(w.exact(q[..., 0], q[..., 1], row["dt"] * row["steps"]))   # FP64 on the GPU
                 row[name + "_l2_err"] = e2
                 row[name + "_linf_err"] = ei
             s.close()

@@ -11,7 +11,8 @@
  * NDG_diffusion_once_matrixForm_Fullyreference: a volume term M^{-1} S^T . F with
  * F = v u - D grad u, and surface terms (J_f / J) LIFT_f (F*.n) whose diffusive part is the
  * normal gradient of the polynomial reconstructed on the enclosed parallelogram of each
- * interior edge (Sec. 4, Algorithm aRDG).  Element-wise D uses Algorithm 2 (D~ = RDG(D1,D2)).
+ * interior edge (Sec. 4, Algorithm aRDG).  Element-wise D enters the edge flux by the paper's
+ * Algorithm 2 (D~ = RDG(D1,D2)) or Algorithm 1 (Sec. 3), chosen at rdg_operator_setup.
  * Time stepping is the three-stage SSP-RK3 scheme.
  *
  * Conventions shared with every caller:
@@ -88,7 +89,9 @@ int rdg_create(rdg_ctx** out, int device, void* cuda_stream);
 /* Free every buffer the context owns and the context itself (NULL is accepted). */
 int rdg_destroy(rdg_ctx* ctx);
 
-/* Mesh: nv vertices xy[2*nv] (x0,y0,x1,y1,...), nt counter-clockwise triangles tri[3*nt]
+/* Mesh (the triangulation of Sec. 3, affine elements of Eq. mapping_tri; the interior edges
+ * are the ones Algorithm aRDG of Sec. 4 reconstructs on): nv vertices xy[2*nv]
+ * (x0,y0,x1,y1,...), nt counter-clockwise triangles tri[3*nt]
  * (0-based vertex ids).  Two faces with the same pair of vertex ids form an edge; the faces
  * left over are matched by coincident midpoints.  bc = RDG_BC_PERIODIC: every face must meet
  * another face whose midpoint agrees modulo period[0..1] (period must be non-NULL); the neighbour's vertex
@@ -100,9 +103,23 @@ int rdg_destroy(rdg_ctx* ctx);
 int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
                     int32_t bc, const double* period);
 
+/* One mesh split across ranks (Sec. 4, Algorithm aRDG: every edge reads all 2 Np values of
+ * both neighbours, so a rank needs the full state of the other ranks' elements next to its
+ * own).  Like rdg_mesh_upload, but triangles [n_owned, nt) are halo copies of elements that
+ * other ranks own: faces of halo triangles that meet no other face become boundary edges
+ * (ghost data zero unless set), so only the rows of halo triangles depend on them; a face of
+ * an owned triangle left unmatched on a periodic mesh is still RDG_EMESH.  Every right-hand
+ * side and stage then computes all nt rows, and the rows [0, n_owned) are exact as long as
+ * the halo rows of each stage's input hold the owners' values (rdg_stage_buffer,
+ * rdg_rows_gather/rdg_rows_scatter, rdg_rk_stage).  Errors: as rdg_mesh_upload, and
+ * RDG_EINVAL for n_owned outside 0..nt. */
+int rdg_mesh_upload_partition(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                              int32_t bc, const double* period, int64_t n_owned);
+
 /* Operators for order N (1..6) with element-wise diffusion D_elem[nt] (> 0), constant
  * velocity (vx, vy), arithmetic precision RDG_FP64, RDG_FP32 or RDG_FP32_3XTF32, interface rule
- * RDG_IFACE_ALG2 or RDG_IFACE_HARMONIC for the edge diffusion coefficient.  Builds, in FP64 on the GPU,
+ * RDG_IFACE_ALG2, RDG_IFACE_ALG1 or RDG_IFACE_HARMONIC for the edge diffusion (Algorithm 1
+ * folds D1 and D2 into the operator in place of D~).  Builds, in FP64 on the GPU,
  * the element metric terms and for every edge the enclosed parallelogram (Sec. 4.2), the
  * projections V^{-1} V_p V_rf^{-1} of both sides (Eq. totalProjection), the least-squares
  * reconstruction (Sec. 4.5) and the edge-normal gradient, folded with D~ = RDG(D1, D2)
@@ -139,7 +156,11 @@ int rdg_get_ghost_coords(rdg_ctx* ctx, double* xy);
 int rdg_set_state(rdg_ctx* ctx, const void* u, int on_device);
 int rdg_get_state(rdg_ctx* ctx, void* out, int to_device);
 
-/* rhs = L(u, t) for device arrays u, rhs [nt][Np] in the context's precision (no host
+/* rhs = L(u, t), the semi-discrete right-hand side of Eq. NDG_diffusion_once_matrixForm_Fullyreference
+ * (Sec. 4.2; volume term M^{-1} S^T . F, surface terms (J_f/J) LIFT_f (F*.n) with the
+ * reconstructed edge gradient of Algorithm aRDG and the interface rule chosen at setup,
+ * plus the source s of Eq. convection_diffusion), for device arrays u, rhs [nt][Np] in the
+ * context's precision (no host
  * synchronisation; enqueued on the context's stream).  Both must be 16-byte aligned and must
  * not overlap (RDG_EINVAL otherwise). */
 int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
@@ -147,13 +168,18 @@ int rdg_rhs_eval(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t);
 /* Allocation-free rhs = L(u, t), for callers that cannot allocate device memory where they
  * evaluate the right-hand side (inside another component's CUDA-graph capture, in loops
  * that must not hit cudaMalloc's implicit synchronisation, or under a pool allocator that
- * owns all device memory).  It computes the same result as rdg_rhs_eval (same kernels) but
- * keeps the per-edge fluxes in one static device array compiled into the library, 8 MiB,
+ * owns all device memory).  It computes the same right-hand side as rdg_rhs_eval, to rounding,
+ * with the unfused pair of kernels (per-edge fluxes, then an element kernel that forms the
+ * volume term, LIFT and sources), and keeps the per-edge fluxes in one static device array
+ * compiled into the library, 8 MiB,
  * held by every GPU that loads the library until the process exits; it calls no allocating
  * routine.  Meshes needing more than 8 MiB of fluxes (n_edges x Nfp x element size) get
  * RDG_EINVAL with a message.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress with the device current); make that first call before any
- * stream capture.  All calls share the array, which keeps the last call's contents (every
+ * address (cudaGetSymbolAddress with the device current) and caches it for the life of the
+ * process, so the address is valid only while that device's primary context lives (not after
+ * a cudaDeviceReset); make that first call before any stream capture.  Contexts using the
+ * GEMM form of the edge flux (RDG_FP32_3XTF32 with N <= 5 and an interface rule other than
+ * RDG_IFACE_ALG1) have no stored operators and get RDG_ESTATE.  All calls share the array, which keeps the last call's contents (every
  * flux is rewritten before it is read, so nothing is cleared): calls whose GPU work
  * overlaps (different streams or devices' contexts sharing a device) race on it.  The paper
  * has no counterpart to this entry point. */
@@ -170,6 +196,26 @@ int rdg_set_integrator(rdg_ctx* ctx, int integrator);
 /* One step of the resident state from time t with step dt with the selected integrator;
  * enqueued, no host synchronisation. */
 int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
+
+/* One stage of one step of the selected integrator from step start t with step dt
+ * (SSP-RK3: stage 0, 1, 2 at t, t+dt, t+dt/2; the low-storage scheme: stages 0..4): the same
+ * launches as the stage inside rdg_rk_step, enqueued.  Stages 0..last in order make one step.
+ * For a mesh split across ranks the caller refreshes the halo rows of rdg_stage_buffer(stage)
+ * before each stage.  Errors: RDG_ESTATE, RDG_EINVAL (stage out of range, bad dt). */
+int rdg_rk_stage(rdg_ctx* ctx, int stage, double t, double dt);
+
+/* Device pointer of the input buffer [nt][Np] of stage `stage` (SSP-RK3: the state, then the
+ * two stage buffers; the low-storage scheme: the state for every stage), owned by the context
+ * and valid until the next rdg_operator_setup or rdg_destroy. */
+int rdg_stage_buffer(rdg_ctx* ctx, int stage, void** dev_ptr);
+
+/* Rows of Np values in the context's precision on the device: gather dst[i][:] =
+ * src[idx[i]][:] or scatter dst[idx[i]][:] = src[i][:] for i < n (idx: device int32).  The
+ * halo exchange of a split mesh: gather the rows a neighbour rank needs into a contiguous
+ * send buffer, scatter received rows into the halo rows.  Indexes outside 0..nt-1 are
+ * skipped and reported by rdg_synchronize.  Enqueued on the context stream. */
+int rdg_rows_gather(rdg_ctx* ctx, const void* src_dev, const int32_t* idx_dev, int64_t n, void* dst_dev);
+int rdg_rows_scatter(rdg_ctx* ctx, const void* src_dev, const int32_t* idx_dev, int64_t n, void* dst_dev);
 
 /* nsteps steps of the selected integrator from t0 with step dt, replayed from a CUDA
  * graph of a fixed chunk of steps (captured on first use for a given dt); enqueued. */
@@ -214,6 +260,28 @@ int rdg_reference_operator(int N, int which, double* out);
  * double), plus per edge (k1, f1, k2, f2) into ids[n_edges][4] (k2 = -1-b for the b-th
  * boundary edge).  For checks and tooling; not needed for solving. */
 int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids);
+
+/* ---- Measurement ---------------------------------------------------------------------------
+ * Points of the error norms: a collapsed Gauss rule on every triangle, exact for total degree
+ * 2N + 4 ((N + 3)^2 points per triangle).  *nq receives the number of points per triangle;
+ * xy (may be NULL) receives their physical coordinates [nt][nq][2] (host, double), where the
+ * caller evaluates the exact solution for rdg_error_norms.  Errors: RDG_ESTATE, RDG_EINVAL. */
+int rdg_error_quadrature(rdg_ctx* ctx, int* nq, double* xy);
+
+/* Error norms of Eq. L2_norm_cellUnit and Eq. Linf_norm_cellUnit (Sec. 5), in FP64 on the GPU:
+ * with e = u - u_e on each triangle k, *l2 = sqrt(sum_k int_k e^2 / sum_k |k|) and *linf =
+ * max_k (1/|k|) int_k |e| (the largest cell mean, as the paper defines its L_inf norm).
+ * u_dev: nodal values [nt][Np] in the context's precision on the device, or NULL for the
+ * resident state; ue_q_dev: the exact solution at the points of rdg_error_quadrature, device
+ * double [nt][nq].  Allocates its scratch on the context stream and waits for it.  Errors:
+ * RDG_ESTATE, RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA. */
+int rdg_error_norms(rdg_ctx* ctx, const void* u_dev, const double* ue_q_dev, double* l2, double* linf);
+
+/* FMA rate of device `device` in FLOP/s (an FMA counts 2) for precision RDG_FP32 or RDG_FP64:
+ * independent FMA chains on every SM, timed with CUDA events, best of four launches after two
+ * warm-up launches, at whatever clocks the GPU runs (nothing is locked or changed).  The
+ * compute side of the right-hand side's roofline.  Errors: RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA. */
+int rdg_peak_fma(int device, int precision, double* flops_per_second);
 
 /* ---- Batched stepping of independent problems ------------------------------------------
  * Many independent solves (different meshes, orders N = 1..6, precisions, dt) advanced

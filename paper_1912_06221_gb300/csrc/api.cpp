@@ -223,17 +223,23 @@ int rdg_destroy(rdg_ctx* ctx) {
   return RDG_OK;
 }
 
-int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri, int32_t bc,
-                    const double* period) {
+}  // extern "C"
+
+// Mesh upload; elements [n_owned, nt) are halo copies of another rank's elements, whose faces
+// may stay unmatched (they become boundary edges that only the halo rows depend on).
+static int mesh_upload_impl(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri, int32_t bc,
+                            const double* period, int64_t n_owned) {
   if (!ctx) return RDG_EINVAL;
   if (nv <= 0 || nt <= 0 || !xy || !tri) return fail(ctx, RDG_EINVAL, "empty mesh or NULL arrays");
   if (nt > (int64_t)1 << 30) return fail(ctx, RDG_EINVAL, "too many triangles (max 2^30)");
   if (bc != RDG_BC_PERIODIC && bc != RDG_BC_DIRICHLET) return fail(ctx, RDG_EINVAL, "bc must be PERIODIC or DIRICHLET");
   if (bc == RDG_BC_PERIODIC && (!period || !(period[0] > 0) || !(period[1] > 0)))
     return fail(ctx, RDG_EINVAL, "periodic mesh needs a positive period");
+  if (n_owned < 0 || n_owned > nt) return fail(ctx, RDG_EINVAL, "n_owned must be in 0..nt");
   free_ops(ctx);
   ctx->mesh_ok = false;
   ctx->K = nt;
+  ctx->n_owned = n_owned;
   ctx->bc = bc;
   ctx->exy.assign(nt * 6, 0.0);
   double hmin = 1e300;
@@ -346,7 +352,7 @@ int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, cons
     const int64_t j = partner[i];
     if (j >= 0 && j < i) continue;
     if (j < 0) {
-      if (bc == RDG_BC_PERIODIC) return fail(ctx, RDG_EMESH, "unmatched face on a periodic mesh");
+      if (bc == RDG_BC_PERIODIC && i / 3 < n_owned) return fail(ctx, RDG_EMESH, "unmatched face on a periodic mesh");
       bnd.push_back(EdgeRec{(int32_t)(i / 3), (int32_t)(i % 3), -1, 1, 0.0, 0.0});
       continue;
     }
@@ -386,6 +392,18 @@ int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, cons
   if (2 * ctx->E > (int64_t)INT32_MAX) return fail(ctx, RDG_EINVAL, "too many edges");
   ctx->mesh_ok = true;
   return RDG_OK;
+}
+
+extern "C" {
+
+int rdg_mesh_upload(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri, int32_t bc,
+                    const double* period) {
+  return mesh_upload_impl(ctx, nv, xy, nt, tri, bc, period, nt);
+}
+
+int rdg_mesh_upload_partition(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tri,
+                              int32_t bc, const double* period, int64_t n_owned) {
+  return mesh_upload_impl(ctx, nv, xy, nt, tri, bc, period, n_owned);
 }
 
 int rdg_mesh_counts(const rdg_ctx* ctx, int64_t* nt, int64_t* n_edges, int64_t* n_boundary) {
@@ -820,6 +838,33 @@ int enqueue_rk_step(rdg_ctx* ctx, const TimeArg& base, double dt) {
   return rc;
 }
 
+// Input buffer of stage `stage` of the selected integrator (SSP-RK3: u, u1, u2; the
+// low-storage scheme updates u in place every stage).
+void* stage_input(rdg_ctx* ctx, int stage) {
+  if (ctx->integrator == RDG_INTEGRATOR_LSRK54) return ctx->d_u;
+  return stage == 0 ? ctx->d_u : (stage == 1 ? ctx->d_u1 : ctx->d_u2);
+}
+
+// One stage of the selected integrator, the same launches as the stage inside
+// enqueue_rk_step (time offsets in units of dt from the step start in base).
+int enqueue_one_stage(rdg_ctx* ctx, int stage, const TimeArg& base, double dt) {
+  TimeArg ts = base;
+  if (ctx->integrator == RDG_INTEGRATOR_LSRK54) {
+    ts.off = base.off + kLsrkC[stage];
+    if (ctx->esz == 4)
+      return enqueue_stage<float>(ctx, ctx->d_u, ctx->d_u1, ctx->d_u, 4, (float)dt, ts, ctx->d_u1, (float)kLsrkA[stage],
+                                  (float)kLsrkB[stage]);
+    return enqueue_stage<double>(ctx, ctx->d_u, ctx->d_u1, ctx->d_u, 4, dt, ts, ctx->d_u1, kLsrkA[stage], kLsrkB[stage]);
+  }
+  static const double off[3] = {0.0, 1.0, 0.5};
+  ts.off = base.off + off[stage];
+  void* in = stage_input(ctx, stage);
+  void* out = stage == 0 ? ctx->d_u1 : (stage == 1 ? ctx->d_u2 : ctx->d_u);
+  const void* un = stage == 0 ? nullptr : ctx->d_u;
+  if (ctx->esz == 4) return enqueue_stage<float>(ctx, in, un, out, stage + 1, (float)dt, ts);
+  return enqueue_stage<double>(ctx, in, un, out, stage + 1, dt, ts);
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
@@ -861,6 +906,47 @@ int rdg_rk_step(rdg_ctx* ctx, double t, double dt) {
   DeviceGuard g(ctx->device);
   TimeArg ta{nullptr, t, dt, 0.0};
   int rc = enqueue_rk_step(ctx, ta, dt);
+  return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_rk_stage(rdg_ctx* ctx, int stage, double t, double dt) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!(dt > 0) || !std::isfinite(t)) return fail(ctx, RDG_EINVAL, "dt must be positive and t finite");
+  const int nst = ctx->integrator == RDG_INTEGRATOR_LSRK54 ? 5 : 3;
+  if (stage < 0 || stage >= nst) return fail(ctx, RDG_EINVAL, "stage out of range for the integrator");
+  DeviceGuard g(ctx->device);
+  TimeArg ta{nullptr, t, dt, 0.0};
+  int rc = enqueue_one_stage(ctx, stage, ta, dt);
+  return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_stage_buffer(rdg_ctx* ctx, int stage, void** dev_ptr) {
+  if (!ctx || !dev_ptr) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  const int nst = ctx->integrator == RDG_INTEGRATOR_LSRK54 ? 5 : 3;
+  if (stage < 0 || stage >= nst) return fail(ctx, RDG_EINVAL, "stage out of range for the integrator");
+  *dev_ptr = stage_input(ctx, stage);
+  return RDG_OK;
+}
+
+int rdg_rows_gather(rdg_ctx* ctx, const void* src_dev, const int32_t* idx_dev, int64_t n, void* dst_dev) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (n < 0 || (n > 0 && (!src_dev || !idx_dev || !dst_dev))) return fail(ctx, RDG_EINVAL, "bad row gather arguments");
+  if (n == 0) return RDG_OK;
+  DeviceGuard g(ctx->device);
+  int rc = launch_rows(ctx->esz, np_of(ctx->N), src_dev, idx_dev, n, dst_dev, false, ctx->K, ctx->d_err, ctx->stream);
+  return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_rows_scatter(rdg_ctx* ctx, const void* src_dev, const int32_t* idx_dev, int64_t n, void* dst_dev) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (n < 0 || (n > 0 && (!src_dev || !idx_dev || !dst_dev))) return fail(ctx, RDG_EINVAL, "bad row scatter arguments");
+  if (n == 0) return RDG_OK;
+  DeviceGuard g(ctx->device);
+  int rc = launch_rows(ctx->esz, np_of(ctx->N), src_dev, idx_dev, n, dst_dev, true, ctx->K, ctx->d_err, ctx->stream);
   return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
 }
 

@@ -28,6 +28,7 @@ struct rdg_ctx {
   // mesh (host)
   bool mesh_ok = false;
   int64_t K = 0, E = 0, B = 0;
+  int64_t n_owned = 0;            // elements [n_owned, K) are halo copies (partitioned upload)
   int bc = 0;
   std::vector<double> exy;       // [K][6]
   std::vector<EdgeRec> edges;    // interior edges first, then boundary edges
@@ -67,4 +68,8 @@ namespace rdg {
 // One SSP-RK3 step of ctx's resident state with every launch on stream s (which may be
 // capturing); used by the batch, whose member steps run on per-member branch streams.
 int enqueue_rk_step_on(rdg_ctx* ctx, cudaStream_t s, const TimeArg& base, double dt);
+// Row gather (dst[i] = src[idx[i]]) or scatter (dst[idx[i]] = src[i]) of np-value rows of
+// esz-byte values; indices outside 0..nrows-1 are recorded in err and skipped.
+int launch_rows(int esz, int np, const void* src, const int32_t* idx, int64_t n, void* dst, bool scatter,
+                int64_t nrows, int* err, cudaStream_t s);
 }  // namespace rdg

@@ -461,6 +461,8 @@ void simplex_basis(int N, double r, double s, double* psi, double* dr, double* d
     }
 }
 
+void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) { gauss_legendre(n, x, w); }
+
 const RefOps* get_refops(int N, const char** err) {
   static const char* kRange = "order N must be in 1..6";
   if (N < 1 || N > kMaxN) { if (err) *err = kRange; return nullptr; }

@@ -54,6 +54,9 @@ struct RefOps {
 // reconstruction system is rank deficient (err receives a message).
 const RefOps* get_refops(int N, const char** err);
 
+// n-point Gauss-Legendre rule on [-1, 1] (Newton iteration on P_n).
+void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w);
+
 // Orthonormal basis on the reference triangle at (r, s): psi[Np]; optionally gradients.
 void simplex_basis(int N, double r, double s, double* psi, double* dpsi_dr, double* dpsi_ds);
 

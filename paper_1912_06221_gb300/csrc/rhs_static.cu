@@ -6,7 +6,9 @@
 // captured), latency-bound loops that must not hit cudaMalloc's implicit synchronisation,
 // and processes whose device memory is owned by a fixed-budget pool allocator.  This entry
 // point uses, instead, one fixed scratch array compiled into the library (kStaticFluxBytes)
-// and calls no allocating routine at all.  The paper has no counterpart to it.
+// and calls no allocating routine at all.  It runs the unfused pair of kernels (edge fluxes
+// into that array, then the element kernel with the volume term, LIFT and sources), not the
+// fused pair of rdg_rhs_eval; the two agree to rounding.  The paper has no counterpart to it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,7 +41,9 @@ extern "C" int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_de
     return fail_static(ctx, RDG_EINVAL, "device arrays must be 16-byte aligned");
   if (u_dev == rhs_dev) return fail_static(ctx, RDG_EINVAL, "u and rhs must not overlap");
   if (ctx->gemm)
-    return fail_static(ctx, RDG_ESTATE, "rdg_rhs_eval_static needs the stored operators (not RDG_FP32_3XTF32)");
+    return fail_static(ctx, RDG_ESTATE,
+                       "rdg_rhs_eval_static needs stored flux operators: contexts using the GEMM form of the edge "
+                       "flux (RDG_FP32_3XTF32 with N <= 5 and an interface rule other than RDG_IFACE_ALG1) are refused");
   const size_t need = (size_t)ctx->E * nfp_of(ctx->N) * ctx->esz;
   if (need > kStaticFluxBytes)
     return fail_static(ctx, RDG_EINVAL,
@@ -53,7 +57,9 @@ extern "C" int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_de
   int rc = RDG_OK;
   void* flux = nullptr;
   {
-    // one-time set-up per device (with that device current): the array's device address
+    // one-time set-up per device (with that device current): the array's device address.
+    // It is cached for the life of the process, so it is valid only while the device's
+    // primary context lives (a cudaDeviceReset by another component would leave it stale).
     std::lock_guard<std::mutex> lk(g_addr_mu);
     if (!g_addr[ctx->device]) {
       void* p = nullptr;

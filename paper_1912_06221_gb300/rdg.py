@@ -35,6 +35,11 @@ SIGNATURES = {
     "rdg_create": (_INT, [ctypes.POINTER(_P), _INT, _P]),
     "rdg_destroy": (_INT, [_P]),
     "rdg_mesh_upload": (_INT, [_P, _I64, _P, _I64, _P, _I32, _P]),
+    "rdg_mesh_upload_partition": (_INT, [_P, _I64, _P, _I64, _P, _I32, _P, _I64]),
+    "rdg_rk_stage": (_INT, [_P, _INT, _D, _D]),
+    "rdg_stage_buffer": (_INT, [_P, _INT, ctypes.POINTER(_P)]),
+    "rdg_rows_gather": (_INT, [_P, _P, _P, _I64, _P]),
+    "rdg_rows_scatter": (_INT, [_P, _P, _P, _I64, _P]),
     "rdg_operator_setup": (_INT, [_P, _INT, _P, _D, _D, _INT, _INT]),
     "rdg_set_forcing": (_INT, [_P, _INT, _P, _P, _P, _INT, _P, _P, _P]),
     "rdg_mesh_counts": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -54,6 +59,9 @@ SIGNATURES = {
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
     "rdg_get_edge_operators": (_INT, [_P, _P, _P]),
     "rdg_set_integrator": (_INT, [_P, _INT]),
+    "rdg_error_quadrature": (_INT, [_P, ctypes.POINTER(_INT), _P]),
+    "rdg_error_norms": (_INT, [_P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "rdg_peak_fma": (_INT, [_INT, _INT, ctypes.POINTER(_D)]),
     "rdg_batch_create": (_INT, [ctypes.POINTER(_P), _INT, _P, _INT]),
     "rdg_batch_destroy": (_INT, [_P]),
     "rdg_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -110,6 +118,13 @@ def query_bytes(N, nt, n_edges, n_boundary, precision, nsrc=0, nghost=0):
     return out.value
 
 
+def peak_fma(device=0, precision=FP32):
+    """FMA rate of the device in FLOP/s (rdg_peak_fma)."""
+    out = _D(0.0)
+    _check(load().rdg_peak_fma(device, precision, ctypes.byref(out)))
+    return out.value
+
+
 def reference_operator(N, which):
     Np, Nfp, Mp = np_of(N), N + 1, (N + 1) ** 2
     shape = {0: (2, Np), 1: (Np, Np), 2: (Np, Np), 3: (Np, 3 * Nfp), 4: (Mp, 2 * Np), 5: (Np, Np),
@@ -123,7 +138,8 @@ class Solver:
     """One library context: mesh, operators of order N and the resident state."""
 
     def __init__(self, xy, tri, N: int, D_elem, v=(0.0, 0.0), bc: int = BC_PERIODIC, period=(1.0, 1.0),
-                 precision: int = FP32, device: int = 0, stream=None, interface: int = IFACE_ALG2):
+                 precision: int = FP32, device: int = 0, stream=None, interface: int = IFACE_ALG2,
+                 n_owned: Optional[int] = None):
         import torch
         self.torch = torch
         self.lib = load()
@@ -139,8 +155,13 @@ class Solver:
         xy = np.ascontiguousarray(xy, np.float64)
         tri = np.ascontiguousarray(tri, np.int32)
         per = np.ascontiguousarray(period if period is not None else (0.0, 0.0), np.float64)
-        self._call("rdg_mesh_upload", xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), bc,
-                   _ptr(per) if period is not None else None)
+        if n_owned is None:
+            self._call("rdg_mesh_upload", xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), bc,
+                       _ptr(per) if period is not None else None)
+        else:   # one part of a mesh split across ranks: triangles n_owned.. are halo copies
+            self._call("rdg_mesh_upload_partition", xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), bc,
+                       _ptr(per) if period is not None else None, int(n_owned))
+        self.n_owned = tri.shape[0] if n_owned is None else int(n_owned)
         D = np.ascontiguousarray(np.broadcast_to(np.asarray(D_elem, np.float64), (tri.shape[0],)))
         self._call("rdg_operator_setup", N, _ptr(D), float(v[0]), float(v[1]), precision, interface)
         K, E, B = _I64(), _I64(), _I64()
@@ -238,6 +259,24 @@ class Solver:
     def rk_step(self, t: float, dt: float):
         self._call("rdg_rk_step", float(t), float(dt))
 
+    def rk_stage(self, stage: int, t: float, dt: float):
+        """One stage of a step from step start t (rdg_rk_stage)."""
+        self._call("rdg_rk_stage", int(stage), float(t), float(dt))
+
+    def stage_buffer(self, stage: int) -> int:
+        """Device address of the input buffer of `stage` (rdg_stage_buffer)."""
+        p = _P()
+        self._call("rdg_stage_buffer", int(stage), ctypes.byref(p))
+        return p.value
+
+    def rows_gather(self, src: int, idx, n: int, dst: int):
+        """dst[i] = src[idx[i]] for i < n (device addresses; idx a CUDA int32 tensor)."""
+        self._call("rdg_rows_gather", _P(src), _P(idx.data_ptr()), int(n), _P(dst))
+
+    def rows_scatter(self, src: int, idx, n: int, dst: int):
+        """dst[idx[i]] = src[i] for i < n (device addresses; idx a CUDA int32 tensor)."""
+        self._call("rdg_rows_scatter", _P(src), _P(idx.data_ptr()), int(n), _P(dst))
+
     def set_integrator(self, kind: int):
         """SSP_RK3 (default) or LSRK54 (the paper's five-stage fourth-order scheme)."""
         self._call("rdg_set_integrator", int(kind))
@@ -254,6 +293,26 @@ class Solver:
 
     def profile(self, enable: bool = True):
         self._call("rdg_profile", 1 if enable else 0)
+
+    # -- error norms (FP64 on the GPU) -------------------------------------------------
+    def error_quadrature(self):
+        """Physical coordinates [K, nq, 2] of the error norms' quadrature points."""
+        nq = _INT(0)
+        self._call("rdg_error_quadrature", ctypes.byref(nq), None)
+        out = np.zeros((self.K, nq.value, 2))
+        self._call("rdg_error_quadrature", ctypes.byref(nq), _ptr(out))
+        return out
+
+    def error_norms(self, exact_q, u=None):
+        """(L2, L_inf of cell means) of u (a CUDA tensor; None: the resident state) against
+        the exact values at the error_quadrature points (array or CUDA tensor [K, nq])."""
+        torch = self.torch
+        ue = exact_q if isinstance(exact_q, torch.Tensor) else torch.tensor(np.asarray(exact_q, np.float64))
+        ue = ue.to(device="cuda:%d" % self.device, dtype=torch.float64).contiguous()
+        l2, li = _D(0.0), _D(0.0)
+        self._call("rdg_error_norms", self._dev_tensor(u) if u is not None else None, _P(ue.data_ptr()),
+                   ctypes.byref(l2), ctypes.byref(li))
+        return l2.value, li.value
 
     def kernel_stats(self, reset: bool = True):
         """{'edge': (launches, ms), 'elem': (launches, ms)} of the event-timed launches."""

@@ -40,7 +40,9 @@ class SolveRequest:
     steps: int
     dt: Optional[float] = None     # None: 0.5 x the stability bound (power iteration)
     precision: int = rdg.FP32
-    interface: int = rdg.IFACE_ALG2
+    # the paper's Algorithm 1: the requests' element-wise D jumps by up to 1e4 across an
+    # interface, where Algorithm 2's operator has growing modes and Algorithm 1's does not
+    interface: int = rdg.IFACE_ALG1
     build: Optional[Callable] = None   # () -> (xy, tri, D_elem), run on the set-up worker
     n_triangles: int = 0           # triangle count when the mesh is built lazily
 

@@ -13,7 +13,7 @@ from synth import unit_square_mesh, random_nodal, PERIODIC, DIRICHLET
 from oracle.mesh import Mesh
 from oracle.rhs import Problem, stable_dt
 
-from tests.test_gpu_parity import TOL, relerr
+from tests.test_gpu_parity import TOL, parity_err, relerr
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -86,7 +86,7 @@ def test_alg1_rhs_parity(N, prec):
     s.rhs_eval(ud, rd, 0.4)
     s.synchronize()
     tol = TOL[rdg.FP64] if prec == rdg.FP64 else TOL[rdg.FP32]
-    assert relerr(rd.cpu().numpy(), pr.rhs(u, 0.4)) < tol
+    assert parity_err(rd.cpu().numpy(), pr.rhs(u, 0.4)) < tol
     s.close()
 
 
@@ -102,5 +102,5 @@ def test_alg1_rk_steps(prec):
     s.solve_to_time(0.0, dt, 21)
     got = s.get_state_host()
     s.synchronize()
-    assert relerr(got, pr.solve(u0, 0.0, dt, 21)) < (1e-10 if prec == rdg.FP64 else 2e-5)
+    assert parity_err(got, pr.solve(u0, 0.0, dt, 21)) < (1e-10 if prec == rdg.FP64 else 2e-5)
     s.close()

@@ -1,0 +1,107 @@
+"""GPU against the FP64 oracle at full size, element by element on sampled elements.
+
+The circle-pulse coefficients (v = (1, 0.5), D = 1 inside the circle r < 0.25 about
+(0.5, 0.5), 1e-4 outside) on a 255 x 255 x 2 jittered periodic mesh: 130050 triangles and
+195075 edges, so the stage kernel's grid (1525 edge blocks and 1017 element blocks, the last
+element tile ragged with 2 elements) runs in more than three waves of its resident blocks on
+152 SMs, with programmatic dependent launch across the waves.  The oracle cannot take the
+whole mesh, so it runs on patches around sampled elements (oracle/patch.py, pinned against
+the full-mesh oracle on CPU): random elements, the first and the ragged last element tiles,
+elements on the periodic boundary and on the D jump.  A right-hand side (both interface
+rules of the paper) and one SSP-RK3 step are compared element by element (largest pointwise
+difference over max |oracle| on the sample) and normwise on the sample.  Tolerances as for
+the other parity tests, FP64 1e-12 and FP32 1e-5, for a random nodal field (whose right-hand
+side is as large as the operator times the field) and for the step.  The right-hand side of
+the smooth pulse is the exception: at h = 1/255 it is a small difference of terms about
+|grad u| / h in size, so its rounding error relative to its own size grows like w / h (w the
+pulse width) times the machine epsilon; there the bounds are 1e-3 (FP32) and 1e-11 (FP64),
+about four times the measured errors."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1912_06221_gb300 as rdg
+from synth import centroids, circle_pulse, random_nodal
+from oracle.patch import PatchProblem, face_neighbours
+
+M = 255
+TOL = {rdg.FP64: 1e-12, rdg.FP32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def work():
+    import __graft_entry__
+    __graft_entry__.build()
+    w = circle_pulse(m=M, N=4)
+    nbr = face_neighbours(w.xy, w.tri)
+    K = w.K
+    rng = np.random.default_rng(12)
+    c = centroids(w.xy, w.tri)
+    h = 1.0 / M
+    r = np.hypot(c[:, 0] - 0.5, c[:, 1] - 0.5)
+    jump = np.flatnonzero(np.abs(r - 0.25) < h)
+    edge = np.flatnonzero((c[:, 0] < h) | (c[:, 0] > 1 - h) | (c[:, 1] < h) | (c[:, 1] > 1 - h))
+    sample = np.unique(np.concatenate([rng.choice(K, 400, replace=False), np.arange(40), np.arange(K - 130, K),
+                                       rng.choice(jump, 60, replace=False), rng.choice(edge, 60, replace=False)]))
+    step_sample = np.unique(np.concatenate([rng.choice(K, 40, replace=False), [0, 1, K - 2, K - 1],
+                                            rng.choice(jump, 12, replace=False)]))
+    return w, nbr, sample, step_sample
+
+
+def _check(got, want, tol):
+    d = np.asarray(got, float) - want
+    ew = np.abs(d).max() / np.abs(want).max()
+    nw = np.linalg.norm(d) / np.linalg.norm(want)
+    print("element-wise %.3e normwise %.3e (tolerance %.0e)" % (ew, nw, tol))
+    assert ew < tol and nw < tol, (ew, nw)
+
+
+@pytest.mark.parametrize("prec", [rdg.FP32, rdg.FP64])
+@pytest.mark.parametrize("iface", [rdg.IFACE_ALG1, rdg.IFACE_ALG2])
+def test_full_size_rhs_sampled_elements(work, prec, iface):
+    w, nbr, sample, _ = work
+    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=prec, interface=iface)
+    assert s.K == 2 * M * M and s.E == 3 * M * M
+    xyn = s.node_coords()
+    name = "alg1" if iface == rdg.IFACE_ALG1 else "alg2"
+    pp = PatchProblem(w.xy, w.tri, w.N, w.D_elem, sample, v=w.v, rings=1, interface=name, nbr=nbr)
+    # the oracle's node coordinates on the sampled elements are the library's
+    assert np.abs(pp.mesh.x[: len(sample)] - xyn[sample, :, 0]).max() < 1e-14
+    smooth_tol = {rdg.FP32: 1e-3, rdg.FP64: 1e-11}
+    for u, tol in ((random_nodal(s.K, s.Np, 31), TOL[prec]), (w.u0(xyn[..., 0], xyn[..., 1]), smooth_tol[prec])):
+        ud = torch.tensor(u, dtype=s.dtype, device="cuda")
+        rd = torch.empty_like(ud)
+        s.rhs_eval(ud, rd, 0.0)
+        s.synchronize()
+        want = pp.rhs(ud.double().cpu().numpy(), 0.0)
+        _check(rd.cpu().numpy()[sample], want, tol)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [rdg.FP32, rdg.FP64])
+def test_full_size_rk3_step_sampled_elements(work, prec):
+    """One SSP-RK3 step (three stages, each two launches; the stage kernel of stage 2 reads the
+    element kernel's output of stage 1 across the whole grid) from the pulse at 0.5 x the
+    stability bound, against the oracle on three-ring patches."""
+    w, nbr, _, step_sample = work
+    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=prec, interface=rdg.IFACE_ALG1)
+    xyn = s.node_coords()
+    u0 = w.u0(xyn[..., 0], xyn[..., 1])
+    # the step size of the workload: 0.5 x 2.5127 / rho, rho from a GPU power iteration
+    x = torch.tensor(random_nodal(s.K, s.Np, 2), dtype=s.dtype, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(30):
+        x /= torch.linalg.vector_norm(x)
+        s.rhs_eval(x, y, 0.0)
+        x, y = y, x
+    dt = 0.5 * 2.5127 / float(torch.linalg.vector_norm(x))
+    ud = torch.tensor(u0, dtype=s.dtype, device="cuda")
+    s.set_state(ud)
+    s.rk_step(0.0, dt)
+    got = s.get_state_host()[step_sample]
+    pp = PatchProblem(w.xy, w.tri, w.N, w.D_elem, step_sample, v=w.v, rings=3, interface="alg1", nbr=nbr)
+    want = pp.rk3_step(ud.double().cpu().numpy(), 0.0, dt)
+    _check(got, want, TOL[prec])
+    s.close()

@@ -19,7 +19,7 @@ from synth import paper_gaussian, unit_square_mesh, random_nodal, DIRICHLET
 from oracle.mesh import Mesh
 from oracle.rhs import Problem, stable_dt, error_norms
 
-from tests.test_gpu_parity import _forcing, relerr
+from tests.test_gpu_parity import _forcing, parity_err, relerr
 from tests.test_oracle_paper_problems import _table
 
 
@@ -51,13 +51,13 @@ def test_lsrk_steps_and_graph_match_oracle(N, prec):
         s.rk_step(t0 + n * dt, dt)
     got = s.get_state_host()
     want = pr.solve(u0, t0, dt, 3, scheme="lsrk54")
-    assert relerr(got, want) < (1e-11 if prec == rdg.FP64 else 1e-5)
+    assert parity_err(got, want) < (1e-11 if prec == rdg.FP64 else 1e-5)
     s.set_state(u0)
     s.solve_to_time(t0, dt, 21)      # one graph chunk of 16 steps and 5 direct steps
     got = s.get_state_host()
     s.synchronize()
     want = pr.solve(u0, t0, dt, 21, scheme="lsrk54")
-    assert relerr(got, want) < (1e-10 if prec == rdg.FP64 else 2e-5)
+    assert parity_err(got, want) < (1e-10 if prec == rdg.FP64 else 2e-5)
     s.close()
 
 
@@ -113,7 +113,7 @@ def test_paper_problem_small_meshes_match_oracle(advection):
         got = s.get_state_host()
         s.synchronize()
         s.close()
-        assert relerr(got, want) < 1e-10
+        assert parity_err(got, want) < 1e-10
 
 
 @pytest.mark.parametrize("N", [1, 2, 3])

@@ -18,7 +18,7 @@ from synth import unit_square_mesh, random_nodal, PERIODIC, DIRICHLET
 from oracle.mesh import Mesh
 from oracle.rhs import Problem, stable_dt
 
-from tests.test_gpu_parity import _forcing, relerr
+from tests.test_gpu_parity import _forcing, parity_err, relerr
 
 TF = rdg.FP32_3XTF32
 
@@ -56,7 +56,7 @@ def test_rhs_parity_tf32(N, bc):
     u = random_nodal(s.K, s.Np, 11)
     u32 = u.astype(np.float32).astype(np.float64)
     got = _rhs(s, u32, 0.37)
-    assert relerr(got, pr.rhs(u32, 0.37)) < 1e-5
+    assert parity_err(got, pr.rhs(u32, 0.37)) < 1e-5
     s.close()
 
 
@@ -74,10 +74,10 @@ def test_tf32_matches_stored_operator_fp32_larger_mesh(N):
         s.set_forcing([], [(np.sin(g[..., 0]) * g[..., 1], rdg.TAU_CONST, 0.0)])
     u = random_nodal(K, a.Np, 4).astype(np.float32).astype(np.float64)
     ra, rb = _rhs(a, u, 0.0), _rhs(b, u, 0.0)
-    assert relerr(ra, rb) < 1e-5
+    assert parity_err(ra, rb) < 1e-5
     me = Mesh(xy, tri, N, bc=DIRICHLET)
     pr = Problem(me, D, v=(0.3, 0.9), ghost_fn=lambda x, y, t: np.sin(x) * y)
-    assert relerr(ra, pr.rhs(u, 0.0)) < 1e-5
+    assert parity_err(ra, pr.rhs(u, 0.0)) < 1e-5
     a.close()
     b.close()
 
@@ -93,7 +93,7 @@ def test_tf32_rk_steps_and_graph(N):
     s.solve_to_time(0.125, dt, 21)
     got = s.get_state_host()
     s.synchronize()
-    assert relerr(got, pr.solve(u0, 0.125, dt, 21)) < 2e-5
+    assert parity_err(got, pr.solve(u0, 0.125, dt, 21)) < 2e-5
     s.close()
 
 
@@ -101,7 +101,13 @@ def test_tf32_order6_uses_stored_operators_and_static_entry_rejects():
     s, me, D, _, _ = _pair(6, 5, PERIODIC)
     pr = Problem(me, D, v=(0.7, -0.4))
     u = random_nodal(s.K, s.Np, 2).astype(np.float32).astype(np.float64)
-    assert relerr(_rhs(s, u, 0.0), pr.rhs(u)) < 1e-5
+    assert parity_err(_rhs(s, u, 0.0), pr.rhs(u)) < 1e-5
+    # order 6 keeps stored operators, so the allocation-free entry point accepts it
+    ud6 = torch.tensor(u, dtype=torch.float32, device="cuda")
+    rd6 = torch.empty_like(ud6)
+    s._call("rdg_rhs_eval_static", rdg.rdg._P(ud6.data_ptr()), rdg.rdg._P(rd6.data_ptr()), 0.0)
+    s.synchronize()
+    assert parity_err(rd6.cpu().numpy(), pr.rhs(u)) < 1e-5
     s.close()
     s4, _, _, _, _ = _pair(4, 5, PERIODIC)
     ud = torch.zeros((s4.K, s4.Np), dtype=torch.float32, device="cuda")

@@ -4,7 +4,8 @@ Parity with the FP64 oracle on meshes of one ragged element tile and of several 
 ragged tail, through every integrator stage kind; then, on a mesh of 157 element tiles (more
 than one per persistent block on 152 SMs, so the blocks loop and prefetch), agreement with
 the FP64 library path, which the parity tests pin to the oracle at every order.  Tolerance:
-FP32 rounding over rows of ~100 terms, 1e-5 normwise as for the other FP32 forms.
+FP32 rounding over rows of ~100 terms, 1e-5 normwise and element-wise as for the other
+FP32 forms.
 """
 import numpy as np
 import pytest
@@ -25,8 +26,7 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def relerr(a, b):
-    return float(np.linalg.norm(np.asarray(a, float) - b) / max(np.linalg.norm(b), 1e-300))
+from tests.test_gpu_parity import parity_err  # noqa: E402  (normwise and element-wise)
 
 
 def _solver(m, prec, bc=PERIODIC, seed=7, v=(0.6, -0.3)):
@@ -51,7 +51,7 @@ def test_order6_fp32_rhs_matches_oracle(m, bc):
     me = Mesh(xy, tri, 6, bc=bc)
     pr = Problem(me, D, v=(0.6, -0.3), ghost_fn=(lambda x, y, t: 0 * x))
     u = random_nodal(s.K, s.Np, 5).astype(np.float32).astype(np.float64)
-    assert relerr(_rhs(s, u), pr.rhs(u)) < 1e-5
+    assert parity_err(_rhs(s, u), pr.rhs(u)) < 1e-5
     s.close()
 
 
@@ -67,7 +67,7 @@ def test_order6_fp32_steps_match_oracle(integrator):
     s.solve_to_time(0.0, dt, n)
     got = s.get_state_host().astype(np.float64)
     want = pr.solve(u0, 0.0, dt, n, scheme="ssp3" if integrator == rdg.SSP_RK3 else "lsrk54")
-    assert relerr(got, want) < 1e-5
+    assert parity_err(got, want) < 1e-5
     s.close()
 
 
@@ -77,10 +77,10 @@ def test_order6_fp32_many_tiles_agrees_with_fp64_path():
     s64, _, _, _ = _solver(100, rdg.FP64, seed=11)
     u = random_nodal(s32.K, s32.Np, 13).astype(np.float32).astype(np.float64)
     r32, r64 = _rhs(s32, u), _rhs(s64, u)
-    assert relerr(r32, r64) < 1e-5
+    assert parity_err(r32, r64) < 1e-5
     # the tail tile's rows and a middle tile's are as accurate as the whole
     for sl in (slice(156 * 128, None), slice(77 * 128, 78 * 128)):
-        assert relerr(r32[sl], r64[sl]) < 1e-5
+        assert parity_err(r32[sl], r64[sl]) < 1e-5
     s32.synchronize()   # raises if a kernel self-check fired
     s32.close()
     s64.close()
