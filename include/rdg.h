@@ -133,6 +133,17 @@ int rdg_mesh_upload_partition(rdg_ctx* ctx, int64_t nv, const double* xy, int64_
 int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision,
                        int interface_rule);
 
+/* rdg_operator_setup for the diagonal diffusion tensor D = (Dx, Dy) of Eq.
+ * NDG_diffusion_once_matrixForm_reference_general (Sec. 3): element-wise Dx[nt], Dy[nt] (> 0),
+ * volume flux F = v u - (Dx u_x, Dy u_y), and on every edge the chosen interface rule applied
+ * per component (Algorithm 2: n . (D~x u~_x, D~y u~_y) with D~x = RDG(Dx1, Dx2) and likewise
+ * for y; Algorithm 1: n . RDG((Dx^1 u~^1_x, Dy^1 u~^1_y), (Dx^2 u~^2_x, Dy^2 u~^2_y)); harmonic:
+ * the per-component harmonic means), folded into the per-edge operators as for scalar D.
+ * Stored operators only: with RDG_FP32_3XTF32 the RDG_FP32 path runs.  Errors: as
+ * rdg_operator_setup (RDG_EINVAL when Dy is NULL). */
+int rdg_operator_setup_aniso(rdg_ctx* ctx, int N, const double* Dx, const double* Dy, double vx, double vy,
+                             int precision, int interface_rule);
+
 /* Separable forcing (after rdg_operator_setup).  Source s(x,t) = sum_m S_m(x) tau_m(t) with
  * S given as nodal values S[nsrc][nt][Np] (host, double), tau_m = 1, cos(w t) or sin(w t)
  * per src_kind[m], src_omega[m].  Dirichlet ghost data g(x,t) = sum_m G_m(x) tau_m(t) with

@@ -133,14 +133,19 @@ class EdgeOps:
         rhs = np.concatenate([uh1, uh2], axis=1)
         return rhs @ self.mesh.ops.Apinv.T
 
-    def edge_normal_gradient(self, c):
-        """g[e, i] = n1 . grad u~ at the diagonal nodes (side 1 face order)."""
+    def edge_gradient(self, c):
+        """(d/dx u~, d/dy u~) [E, Nfp] at the diagonal nodes (side 1 face order)."""
         ops = self.mesh.ops
         dR = c @ ops.DR.T
         dS = c @ ops.DS.T
         Rx, Ry, Sx, Sy = self.Rx.T
         ux = Rx[:, None] * dR + Sx[:, None] * dS
         uy = Ry[:, None] * dR + Sy[:, None] * dS
+        return ux, uy
+
+    def edge_normal_gradient(self, c):
+        """g[e, i] = n1 . grad u~ at the diagonal nodes (side 1 face order)."""
+        ux, uy = self.edge_gradient(c)
         return self.n1[:, 0:1] * ux + self.n1[:, 1:2] * uy
 
     def reconstructed_values(self, c):
@@ -159,7 +164,10 @@ class EdgeOps:
         Grad - nodal gradient of u~^k on Omega'_k in physical coordinates, d/dR = +-d/dr.
         Product - D_p^k grad u~^k at the sub-triangle nodes.
         RDG - least-squares reconstruction of each component from the two sub-triangles'
-        modal data, evaluated at the diagonal nodes; then n1 . (.)."""
+        modal data, evaluated at the diagonal nodes; then n1 . (.).
+
+        D1, D2 are [E] (isotropic) or [E, 2] (the diagonal tensor (Dx, Dy) of Eq.
+        NDG_diffusion_once_matrixForm_reference_general: component x of the product uses Dx)."""
         ops = self.mesh.ops
         Rx, Ry, Sx, Sy = self.Rx.T
         Phi = ops.phi(ops.diag_R, ops.diag_S)
@@ -174,7 +182,9 @@ class EdgeOps:
                 dr = nod @ ops.Dr.T
                 ds = nod @ ops.Ds.T
                 g = sgn * (dRphys[:, None] * dr + dSphys[:, None] * ds)
-                w = np.asarray(Dk)[:, None] * g     # Product with D_p^k
+                Dc = np.asarray(Dk)
+                Dc = Dc[:, comp] if Dc.ndim == 2 else Dc
+                w = Dc[:, None] * g                 # Product with D_p^k (component comp)
                 modal.append(w @ ops.Vinv.T)        # modal data of the component on Omega'_k
             cc = np.concatenate(modal, axis=1) @ ops.Apinv.T   # RDG of the component
             out += self.n1[:, comp:comp + 1] * (cc @ Phi.T)

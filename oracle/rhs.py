@@ -52,6 +52,10 @@ class Problem:
     """A mesh plus coefficients: D per element, constant velocity v, optional separable
     source and Dirichlet ghost data (lists of (nodal profile, kind, omega)).
 
+    D_elem: [K] for isotropic diffusion, or [K, 2] for the diagonal tensor D = (Dx, Dy) of Eq.
+    NDG_diffusion_once_matrixForm_reference_general (the volume flux is (Dx u_x, Dy u_y); the
+    interface rules below act on each component).
+
     interface: how the edge diffusion coefficient D~ is formed for element-wise D.
       "alg1"      the paper's Algorithm 1: the edge flux is n . RDG(D_p^1 grad u~^1,
                   D_p^2 grad u~^2) with Separation read as the L2 projection of u~ onto
@@ -75,18 +79,24 @@ class Problem:
         self.k2 = np.array([e[2] for e in m.edges])
         self.f2 = np.array([e[3] for e in m.edges])
         self.interior = self.k2 >= 0
-        D2 = np.where(self.interior, self.D[np.maximum(self.k2, 0)], self.D[self.k1])
+        self.aniso = self.D.ndim == 2
+        if self.aniso and self.D.shape[1] != 2:
+            raise ValueError("D_elem must be [K] or [K, 2]")
+        inner = self.interior[:, None] if self.aniso else self.interior
+        D2 = np.where(inner, self.D[np.maximum(self.k2, 0)], self.D[self.k1])
         self.interface = interface
         self.D1e, self.D2e = self.D[self.k1], D2
+        comps = [(self.D1e[:, c], D2[:, c]) for c in range(2)] if self.aniso else [(self.D1e, D2)]
         if interface == "alg1":
             self.Dt = None
         elif interface == "alg2":
-            self.Dt = self.eops.reconstruct_D(self.D[self.k1], D2)
+            self.Dt = [self.eops.reconstruct_D(a, b) for a, b in comps]
         elif interface == "harmonic":
-            D1 = self.D[self.k1]
-            self.Dt = np.repeat((2 * D1 * D2 / (D1 + D2))[:, None], mesh.ops.Nfp, axis=1)
+            self.Dt = [np.repeat((2 * a * b / (a + b))[:, None], mesh.ops.Nfp, axis=1) for a, b in comps]
         else:
             raise ValueError(interface)
+        if not self.aniso and self.Dt is not None:
+            self.Dt = self.Dt[0]
         self.bnd = np.flatnonzero(~self.interior)
         self.ghost_xy = [m.ghost_nodes(e) for e in self.bnd]
 
@@ -109,6 +119,9 @@ class Problem:
         c = self.eops.reconstruct(u1, u2)
         if self.interface == "alg1":
             Dg = self.eops.flux_algorithm1(c, self.D1e, self.D2e)
+        elif self.aniso:
+            ux, uy = self.eops.edge_gradient(c)       # n1 . (D~x u~_x, D~y u~_y)
+            Dg = self.eops.n1[:, 0:1] * self.Dt[0] * ux + self.eops.n1[:, 1:2] * self.Dt[1] * uy
         else:
             Dg = self.Dt * self.eops.edge_normal_gradient(c)
         # upwind convective trace
@@ -122,13 +135,14 @@ class Problem:
     def rhs(self, u, t=0.0):
         m = self.mesh
         ops = m.ops
-        D = self.D[:, None]
+        Dx = (self.D[:, 0] if self.aniso else self.D)[:, None]
+        Dy = (self.D[:, 1] if self.aniso else self.D)[:, None]
         ur = u @ ops.Dr.T
         us = u @ ops.Ds.T
         ux = m.rx[:, None] * ur + m.sx[:, None] * us
         uy = m.ry[:, None] * ur + m.sy[:, None] * us
-        Fx = self.v[0] * u - D * ux
-        Fy = self.v[1] * u - D * uy
+        Fx = self.v[0] * u - Dx * ux
+        Fy = self.v[1] * u - Dy * uy
         # volume term M^{-1} S^T . F  (S = J r_x S_ref, the J cancels with M^k = J M)
         Fr = m.rx[:, None] * Fx + m.ry[:, None] * Fy
         Fs = m.sx[:, None] * Fx + m.sy[:, None] * Fy

@@ -449,7 +449,8 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
     sh[2 * e + 1] = ctx->edges[e].shy;
   }
   std::vector<double> refs = pack_setup_refs(*o);
-  double *d_xy = nullptr, *d_sh = nullptr, *d_D = nullptr, *d_refs = nullptr;
+  double *d_xy = nullptr, *d_sh = nullptr, *d_D = nullptr, *d_Dy = nullptr, *d_refs = nullptr;
+  const bool aniso = !ctx->Dy.empty();
   int32_t *d_i = nullptr;
   int rc = RDG_OK;
   cudaError_t e;
@@ -458,6 +459,7 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
     dfree(d_xy, s);
     dfree(d_sh, s);
     dfree(d_D, s);
+    dfree(d_Dy, s);
     dfree(d_refs, s);
     dfree(d_i, s);
     cudaStreamSynchronize(s);
@@ -465,6 +467,7 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
   if ((e = dalloc(&d_xy, K * 6 * sizeof(double), s)) != cudaSuccess ||
       (e = dalloc(&d_sh, 2 * E * sizeof(double), s)) != cudaSuccess ||
       (e = dalloc(&d_D, K * sizeof(double), s)) != cudaSuccess ||
+      (aniso && (e = dalloc(&d_Dy, K * sizeof(double), s)) != cudaSuccess) ||
       (e = dalloc(&d_refs, refs.size() * sizeof(double), s)) != cudaSuccess ||
       (e = dalloc(&d_i, 4 * E * sizeof(int32_t), s)) != cudaSuccess) {
     cleanup();
@@ -473,6 +476,8 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
   if ((e = cudaMemcpyAsync(d_xy, ctx->exy.data(), K * 6 * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_sh, sh.data(), 2 * E * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_D, ctx->Dk.data(), K * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (aniso && (e = cudaMemcpyAsync(d_Dy, ctx->Dy.data(), K * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+                    cudaSuccess) ||
       (e = cudaMemcpyAsync(d_refs, refs.data(), refs.size() * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_i, k1.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_i + E, f1.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -487,11 +492,11 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
       return cuda_fail(ctx, e, "W clear");
     }
   }
-  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_refs, E, ctx->vx, ctx->vy, ctx->iface,
-                 (int64_t)refs.size()};
+  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_Dy, d_refs, E, ctx->vx, ctx->vy,
+                 ctx->iface, (int64_t)refs.size()};
   rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, P_tiled, s);
   if (rc == RDG_OK && ctx->d_geo && !W_dense)
-    rc = setup_elements(K, d_xy, d_D, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
+    rc = setup_elements(K, d_xy, d_D, d_Dy, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
   e = cudaStreamSynchronize(s);
   cleanup();
   if (rc != RDG_OK) return fail(ctx, rc, "setup kernel launch failed");
@@ -501,8 +506,12 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
 
 extern "C" {
 
-int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision,
-                       int interface_rule) {
+}  // extern "C"
+
+// Operator set-up; Dy (may be null) is the y diffusion of a diagonal tensor (D_elem then
+// holds the x diffusion), which needs the stored operators.
+static int operator_setup_impl(rdg_ctx* ctx, int N, const double* D_elem, const double* Dy, double vx, double vy,
+                               int precision, int interface_rule) {
   if (!ctx) return RDG_EINVAL;
   if (!ctx->mesh_ok) return fail(ctx, RDG_ESTATE, "rdg_mesh_upload must come first");
   if (N < 1 || N > kMaxN) return fail(ctx, RDG_EINVAL, "order N must be in 1..6");
@@ -513,7 +522,8 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
     return fail(ctx, RDG_EINVAL, "interface rule must be RDG_IFACE_ALG2, RDG_IFACE_HARMONIC or RDG_IFACE_ALG1");
   if (!std::isfinite(vx) || !std::isfinite(vy)) return fail(ctx, RDG_EINVAL, "velocity not finite");
   for (int64_t k = 0; k < ctx->K; ++k)
-    if (!(D_elem[k] > 0) || !std::isfinite(D_elem[k])) return fail(ctx, RDG_EINVAL, "D must be positive and finite");
+    if (!(D_elem[k] > 0) || !std::isfinite(D_elem[k]) || (Dy && (!(Dy[k] > 0) || !std::isfinite(Dy[k]))))
+      return fail(ctx, RDG_EINVAL, "D must be positive and finite");
   const char* msg = "";
   const RefOps* o = get_refops(N, &msg);
   if (!o) return fail(ctx, RDG_ERANK, msg);
@@ -522,11 +532,13 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   ctx->N = N;
   ctx->prec = precision;
   ctx->esz = precision == RDG_FP64 ? 8 : 4;
-  ctx->gemm = uses_gemm(N, precision, interface_rule);
+  ctx->gemm = uses_gemm(N, precision, interface_rule) && !Dy;   // the GEMM form folds one isotropic D~
   ctx->vx = vx;
   ctx->vy = vy;
   ctx->iface = interface_rule;
   ctx->Dk.assign(D_elem, D_elem + ctx->K);
+  if (Dy) ctx->Dy.assign(Dy, Dy + ctx->K);
+  else ctx->Dy.clear();
   const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
   const int64_t stb = K * Np * esz;
   CK(dalloc(&ctx->d_W, ctx->gemm ? edge_data_bytes(N, E, precision) : w_bytes(N, E, (int)esz), ctx->stream));
@@ -560,6 +572,19 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
   }
   ctx->ops_ok = true;
   return RDG_OK;
+}
+
+extern "C" {
+
+int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, double vy, int precision,
+                       int interface_rule) {
+  return operator_setup_impl(ctx, N, D_elem, nullptr, vx, vy, precision, interface_rule);
+}
+
+int rdg_operator_setup_aniso(rdg_ctx* ctx, int N, const double* Dx, const double* Dy, double vx, double vy,
+                             int precision, int interface_rule) {
+  if (ctx && !Dy) return fail(ctx, RDG_EINVAL, "Dy is NULL");
+  return operator_setup_impl(ctx, N, Dx, Dy, vx, vy, precision, interface_rule);
 }
 
 int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids) {

@@ -37,7 +37,8 @@ struct rdg_ctx {
   bool ops_ok = false;
   int N = 0, prec = RDG_FP32, esz = 4, iface = RDG_IFACE_ALG2;
   double vx = 0, vy = 0;
-  std::vector<double> Dk;
+  std::vector<double> Dk;           // element diffusion (x diffusion when Dy is set)
+  std::vector<double> Dy;           // y diffusion of a diagonal tensor (Dx, Dy); empty: isotropic
   // device buffers
   int integrator = RDG_INTEGRATOR_SSP_RK3;
   bool gemm = false;                // GEMM form of the edge flux (RDG_FP32_3XTF32, N <= kMaxGemmN)

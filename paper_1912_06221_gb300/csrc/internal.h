@@ -124,7 +124,8 @@ struct EdgeSetupIn {
   const int32_t* k2;       // -1-b for boundary edge b
   const int32_t* f2;
   const double* shift;     // [E][2]
-  const double* D;         // [K]
+  const double* D;         // [K] (x diffusion when Dy is set)
+  const double* Dy;        // [K] y diffusion of the diagonal tensor (Dx, Dy), or null: isotropic
   const double* refs;      // per-order reference constants (layout in setup.cu)
   int64_t E;
   double vx, vy;
@@ -136,7 +137,8 @@ struct EdgeSetupIn {
 // (W_dense), and/or the GEMM-form parameter record (P_tiled, FP32); any may be null.
 int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, double* W_dense, float* P_tiled,
                 cudaStream_t s);
-int setup_elements(int64_t K, const double* xy, const double* D, double vx, double vy, void* geo, int elem_bytes,
+int setup_elements(int64_t K, const double* xy, const double* D, const double* Dy, double vx, double vy, void* geo,
+                   int elem_bytes,
                    cudaStream_t s);
 // Reference constants for the setup kernel, flattened in the order setup.cu reads them.
 std::vector<double> pack_setup_refs(const RefOps& o);

@@ -204,17 +204,21 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   const D2 e2 = mk(x1[2 * fb[f1]], x1[2 * fb[f1] + 1]);
   const D2 q1 = mk(x1[2 * fc[f1]], x1[2 * fc[f1] + 1]);
   D2 q2;
-  double D2v;
+  double D2v, D2y;
+  const bool aniso = in.Dy != nullptr;   // diagonal tensor (Dx, Dy); D holds Dx
   if (k2 >= 0) {
     const double* x2 = in.xy + (int64_t)k2 * 6;
     q2 = mk(x2[2 * fc[f2]] + in.shift[2 * e], x2[2 * fc[f2] + 1] + in.shift[2 * e + 1]);
     D2v = in.D[k2];
+    D2y = aniso ? in.Dy[k2] : D2v;
   } else {
     q2 = (e1 + e2) - q1;   // ghost: point reflection of element k1 about the edge midpoint
     f2 = 1;                // the ghost's hypotenuse is the shared edge
     D2v = in.D[k1];
+    D2y = aniso ? in.Dy[k1] : D2v;
   }
   const double D1v = in.D[k1];
+  const double D1y = aniso ? in.Dy[k1] : D1v;
   const D2 p1 = parallelogram_apex(e1, e2, q1, q2);
   const D2 p2 = (e1 + e2) - p1;
   double al[2], be[2];
@@ -267,11 +271,29 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
     }
     const double* QRV = QV + (2 * side) * NFP * NP;
     const double* QSV = QV + (2 * side + 1) * NFP * NP;
-    if (in.iface == RDG_IFACE_ALG1) {
+    if (in.iface == RDG_IFACE_ALG1 && aniso) {
+      // Algorithm 1 with D = (Dx, Dy): sub-triangle j's product is (Dx^j u~_x, Dy^j u~_y), so its
+      // R and S parts carry n_x Dx^j R_x + n_y Dy^j R_y and n_x Dx^j S_x + n_y Dy^j S_y
+      const double* Z = zq + side * 4 * NFP * NP;
+      const double aR1 = n1.x * D1v * Rx + n1.y * D1y * Ry, aS1 = n1.x * D1v * Sx + n1.y * D1y * Sy;
+      const double aR2 = n1.x * D2v * Rx + n1.y * D2y * Ry, aS2 = n1.x * D2v * Sx + n1.y * D2y * Sy;
+      for (int t = lane; t < NFP * NP; t += 32)
+        sK[warp][t] = aR1 * Z[t] + aS1 * Z[NFP * NP + t] + aR2 * Z[2 * NFP * NP + t] + aS2 * Z[3 * NFP * NP + t];
+    } else if (in.iface == RDG_IFACE_ALG1) {
       // Algorithm 1: D_1 (kR ZR[0] + kS ZS[0]) + D_2 (kR ZR[1] + kS ZS[1]) for this side
       const double* Z = zq + side * 4 * NFP * NP;
       for (int t = lane; t < NFP * NP; t += 32)
         sK[warp][t] = D1v * (kR * Z[t] + kS * Z[NFP * NP + t]) + D2v * (kR * Z[2 * NFP * NP + t] + kS * Z[3 * NFP * NP + t]);
+    } else if (aniso) {
+      // Algorithm 2 (or the harmonic rule) per component: n1 . (D~x u~_x, D~y u~_y) at diagonal
+      // node i, i.e. row i carries n_x D~x_i R_x + n_y D~y_i R_y and the same with S
+      for (int t = lane; t < NFP * NP; t += 32) {
+        const int i = t / NP;
+        const bool hm = in.iface == RDG_IFACE_HARMONIC;
+        const double Dtx = hm ? 2.0 * D1v * D2v / (D1v + D2v) : D1v * dvec[i] + D2v * dvec[NFP + i];
+        const double Dty = hm ? 2.0 * D1y * D2y / (D1y + D2y) : D1y * dvec[i] + D2y * dvec[NFP + i];
+        sK[warp][t] = (n1.x * Dtx * Rx + n1.y * Dty * Ry) * QRV[t] + (n1.x * Dtx * Sx + n1.y * Dty * Sy) * QSV[t];
+      }
     } else {
       for (int t = lane; t < NFP * NP; t += 32) sK[warp][t] = kR * QRV[t] + kS * QSV[t];
     }
@@ -291,7 +313,7 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
 #pragma unroll 7
       for (int j = 0; j < NP; ++j) c = fma(sB[warp][i * NP + j], Vinv[j * NP + l], c);
       const int col = (int)perminv[f * NP + l];
-      const double Dt = in.iface == RDG_IFACE_ALG1       ? 1.0   // D inside the factors
+      const double Dt = (in.iface == RDG_IFACE_ALG1 || aniso) ? 1.0   // D inside the factors
                         : in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
                                                          : D1v * dvec[i] + D2v * dvec[NFP + i];
       double w = -Jf * Dt * c;
@@ -323,8 +345,8 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   }
 }
 
-__global__ void elem_setup_kernel(int64_t K, const double* xy, const double* D, double vx, double vy, void* geo,
-                                  int elem_bytes) {
+__global__ void elem_setup_kernel(int64_t K, const double* xy, const double* D, const double* Dy, double vx, double vy,
+                                  void* geo, int elem_bytes) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   const double* v = xy + k * 6;
@@ -332,9 +354,16 @@ __global__ void elem_setup_kernel(int64_t K, const double* xy, const double* D, 
   const double xs = 0.5 * (v[4] - v[0]), ys = 0.5 * (v[5] - v[1]);
   const double J = xr * ys - xs * yr;
   const double rx = ys / J, ry = -xs / J, sx = -yr / J, sy = xr / J;
-  const double Dk = D[k];
-  const double g[6] = {rx * vx + ry * vy, sx * vx + sy * vy, Dk * (rx * rx + ry * ry), Dk * (rx * sx + ry * sy),
-                       Dk * (sx * sx + sy * sy), 1.0 / J};
+  // F_r = r . F, F_s = s . F with F = v u - (Dx u_x, Dy u_y): g_ab = Dx a_x b_x + Dy a_y b_y
+  const double Dx = D[k];
+  double g[6] = {rx * vx + ry * vy, sx * vx + sy * vy, Dx * (rx * rx + ry * ry), Dx * (rx * sx + ry * sy),
+                 Dx * (sx * sx + sy * sy), 1.0 / J};
+  if (Dy) {
+    const double Dyk = Dy[k];
+    g[2] = Dx * rx * rx + Dyk * ry * ry;
+    g[3] = Dx * rx * sx + Dyk * ry * sy;
+    g[4] = Dx * sx * sx + Dyk * sy * sy;
+  }
   for (int c = 0; c < 6; ++c) {
     if (elem_bytes == 4) static_cast<float*>(geo)[c * K + k] = (float)g[c];
     else static_cast<double*>(geo)[c * K + k] = g[c];
@@ -373,10 +402,10 @@ int setup_edges(int N, const EdgeSetupIn& in, void* W_tiled, int elem_bytes, dou
   }
 }
 
-int setup_elements(int64_t K, const double* xy, const double* D, double vx, double vy, void* geo, int elem_bytes,
-                   cudaStream_t s) {
+int setup_elements(int64_t K, const double* xy, const double* D, const double* Dy, double vx, double vy, void* geo,
+                   int elem_bytes, cudaStream_t s) {
   if (K == 0) return RDG_OK;
-  elem_setup_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(K, xy, D, vx, vy, geo, elem_bytes);
+  elem_setup_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(K, xy, D, Dy, vx, vy, geo, elem_bytes);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
 

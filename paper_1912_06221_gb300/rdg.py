@@ -41,6 +41,7 @@ SIGNATURES = {
     "rdg_rows_gather": (_INT, [_P, _P, _P, _I64, _P]),
     "rdg_rows_scatter": (_INT, [_P, _P, _P, _I64, _P]),
     "rdg_operator_setup": (_INT, [_P, _INT, _P, _D, _D, _INT, _INT]),
+    "rdg_operator_setup_aniso": (_INT, [_P, _INT, _P, _P, _D, _D, _INT, _INT]),
     "rdg_set_forcing": (_INT, [_P, _INT, _P, _P, _P, _INT, _P, _P, _P]),
     "rdg_mesh_counts": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "rdg_get_node_coords": (_INT, [_P, _P]),
@@ -162,8 +163,15 @@ class Solver:
             self._call("rdg_mesh_upload_partition", xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), bc,
                        _ptr(per) if period is not None else None, int(n_owned))
         self.n_owned = tri.shape[0] if n_owned is None else int(n_owned)
-        D = np.ascontiguousarray(np.broadcast_to(np.asarray(D_elem, np.float64), (tri.shape[0],)))
-        self._call("rdg_operator_setup", N, _ptr(D), float(v[0]), float(v[1]), precision, interface)
+        Da = np.asarray(D_elem, np.float64)
+        if Da.ndim == 2:        # [nt, 2]: the diagonal tensor (Dx, Dy)
+            Dx = np.ascontiguousarray(Da[:, 0])
+            Dy = np.ascontiguousarray(Da[:, 1])
+            self._call("rdg_operator_setup_aniso", N, _ptr(Dx), _ptr(Dy), float(v[0]), float(v[1]), precision,
+                       interface)
+        else:
+            D = np.ascontiguousarray(np.broadcast_to(Da, (tri.shape[0],)))
+            self._call("rdg_operator_setup", N, _ptr(D), float(v[0]), float(v[1]), precision, interface)
         K, E, B = _I64(), _I64(), _I64()
         self._call("rdg_mesh_counts", ctypes.byref(K), ctypes.byref(E), ctypes.byref(B))
         self.K, self.E, self.B = K.value, E.value, B.value

@@ -12,10 +12,12 @@ rules of the paper) and one SSP-RK3 step are compared element by element (larges
 difference over max |oracle| on the sample) and normwise on the sample.  Tolerances as for
 the other parity tests, FP64 1e-12 and FP32 1e-5, for a random nodal field (whose right-hand
 side is as large as the operator times the field) and for the step.  The right-hand side of
-the smooth pulse is the exception: at h = 1/255 it is a small difference of terms about
-|grad u| / h in size, so its rounding error relative to its own size grows like w / h (w the
-pulse width) times the machine epsilon; there the bounds are 1e-3 (FP32) and 1e-11 (FP64),
-about four times the measured errors."""
+the smooth pulse is the exception: at h = 1/255 it is a small difference of terms some 1e4
+times larger (of size |grad u| / h against |lap u|), so a relative error delta in the
+operator's entries shows up multiplied by that factor: FP32 storage (delta ~ 6e-8) gives
+about 3e-4, and both FP64 constructions (GPU and oracle, delta ~ 1e-13) agree to about 2e-9
+(measured).  There the bounds are 1e-3 (FP32) and 1e-8 (FP64); the step from the same pulse,
+whose increment dt L u is small beside u, meets the strict tolerances."""
 import numpy as np
 import pytest
 
@@ -69,7 +71,7 @@ def test_full_size_rhs_sampled_elements(work, prec, iface):
     pp = PatchProblem(w.xy, w.tri, w.N, w.D_elem, sample, v=w.v, rings=1, interface=name, nbr=nbr)
     # the oracle's node coordinates on the sampled elements are the library's
     assert np.abs(pp.mesh.x[: len(sample)] - xyn[sample, :, 0]).max() < 1e-14
-    smooth_tol = {rdg.FP32: 1e-3, rdg.FP64: 1e-11}
+    smooth_tol = {rdg.FP32: 1e-3, rdg.FP64: 1e-8}
     for u, tol in ((random_nodal(s.K, s.Np, 31), TOL[prec]), (w.u0(xyn[..., 0], xyn[..., 1]), smooth_tol[prec])):
         ud = torch.tensor(u, dtype=s.dtype, device="cuda")
         rd = torch.empty_like(ud)

@@ -17,7 +17,7 @@ import paper_1912_06221_gb300 as rdg
 from paper_1912_06221_gb300.partition import SplitSolver, build_plan, face_adjacency, rcb_partition
 from synth import random_nodal, unit_square_mesh
 from oracle.mesh import Mesh
-from oracle.rhs import Problem
+from oracle.rhs import Problem, stable_dt
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -67,7 +67,9 @@ def test_split_mesh_steps_equal_unsplit(world, prec, bc):
     for sp in parts:
         sp.set_owned_state(u0)
     whole.set_state(u0)
-    dt, nsteps = 2e-4, 10
+    me = Mesh(xy, tri, N, bc=bc)
+    pr = Problem(me, D, v=v, interface="alg1", ghost_fn=(lambda x, y, t: 0.0 * x) if bc == rdg.BC_DIRICHLET else None)
+    dt, nsteps = stable_dt(pr, 0.5, 20), 10
     for n in range(nsteps):
         for st in range(3):
             _exchange_all(parts, st)
@@ -78,9 +80,8 @@ def test_split_mesh_steps_equal_unsplit(world, prec, bc):
     for sp in parts:
         got[sp.plan.elements[: sp.n_owned]] = sp.owned_state()
         sp.s.synchronize()
-    me = Mesh(xy, tri, N, bc=bc)
-    pr = Problem(me, D, v=v, interface="alg1", ghost_fn=(lambda x, y, t: 0.0 * x) if bc == rdg.BC_DIRICHLET else None)
     want = pr.solve(u0, 0.0, dt, nsteps)
+    assert np.abs(want).max() < 10 * np.abs(u0).max()      # a stable step: nothing grows
     tol = 1e-10 if prec == rdg.FP64 else 1e-5
     assert _err(got, want) < tol
     assert _err(got, whole.get_state_host()) < tol

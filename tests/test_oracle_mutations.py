@@ -161,3 +161,29 @@ def test_mutation_lsrk_weight(monkeypatch):
     bad[3], bad[4] = bad[4], bad[3]
     monkeypatch.setattr(orhs, "LSRK_B", tuple(bad))
     _fails(TL.test_lsrk_local_error_is_fifth_order)
+
+
+def test_mutation_tensor_components_swapped_on_edges(monkeypatch):
+    """Algorithm 2 with D = (Dx, Dy) applying D~y to u~_x and D~x to u~_y on the edges."""
+    from tests import test_oracle_aniso as TN
+    orig = ardg.EdgeOps.edge_gradient
+
+    def bad(self, c):
+        ux, uy = orig(self, c)
+        return uy, ux
+    monkeypatch.setattr(ardg.EdgeOps, "edge_gradient", bad)
+    _fails(TN.test_tensor_rotation_swaps_components, "alg2")
+
+
+def test_mutation_tensor_volume_uses_one_component(monkeypatch):
+    """The volume flux with Dx in both components."""
+    from tests import test_oracle_aniso as TN
+    orig = orhs.Problem.__init__
+
+    def bad(self, mesh, D_elem, *a, **k):
+        orig(self, mesh, D_elem, *a, **k)
+        if self.aniso:
+            self.D = self.D.copy()
+            self.D[:, 1] = self.D[:, 0]
+    monkeypatch.setattr(orhs.Problem, "__init__", bad)
+    _fails(TN.test_tensor_sin_mode_decay_rate, "alg1")
