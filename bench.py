@@ -137,7 +137,7 @@ class ClockSampler:
 
 
 TRAFFIC_CSV = os.path.join(ROOT, "profiles", "stage_kernels_circle_pulse_N4_m256_fp32_dram.csv")
-STAGE_SOURCES = ("rhs_kernels.cuh", "rhs_order.cu", "internal.h")
+STAGE_SOURCES = ("rhs_kernels.cuh", "rhs_order.cu")     # the stage and element kernels' code
 
 
 def stage_source_hash():
@@ -400,7 +400,8 @@ def run_ours(args):
     elem_avg = elem_ms / elem_n
     ach = stage_alg / (edge_avg / 1e3) / 1e9
     traffic, traffic_src = (None, "GEMM form: no capture") if gemm else profiled_traffic(args)
-    roof = {"bound": "hbm", "kernel": "edge_gemm_kernel<4>" if gemm else "edge_flux_kernel<float,4,VOL=1>",
+    kname = "edge_gemm_kernel<4>" if gemm else "edge_flux_kernel<float,4,VOL=1>"
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind, "traffic": traffic,
             "traffic_source": traffic_src,
@@ -409,9 +410,9 @@ def run_ours(args):
                               % alg_bytes_per_element(N_ORDER, 4),
             "avg_launch_us": edge_avg * 1e3,
             "share_of_kernel_time": edge_ms / (edge_ms + elem_ms),
-            "kernel_own_bytes": {"edge_flux_kernel": edge_bytes, "elem_lite_kernel": elem_bytes,
-                                 "note": "each kernel's own reads and writes, volume-term and face-flux round "
-                                         "trips included (most of them hit L2 in steady state)"},
+            "kernel_own_bytes": {"edge_and_volume_blocks": edge_bytes, "element_updates": elem_bytes,
+                                 "note": "reads and writes of the stage's two parts, volume-term and face-flux "
+                                         "round trips included (they mostly hit L2 in steady state)"},
             "elem_kernel": {"name": "elem_lite_kernel<float,4,MODE>", "avg_launch_us": elem_avg * 1e3}}
     # the whole stage inside the replayed graph (programmatic dependent launch): the same
     # algorithmic bytes over the timed solve's time per stage
@@ -636,9 +637,10 @@ def run_batch(args):
     """64 independent periodic heat problems (seed 2): mesh side uniform in 8..256 cells
     (2 triangles per cell, 10% jitter), N uniform in 1..6, D log-uniform in [1e-3, 1], random
     low-mode Fourier u0, 100 SSP-RK3 steps each at 0.5 x its stability bound, FP32, all
-    members stepped together by the library's batch (one CUDA graph of parallel per-member
-    branches, replayed per chunk of steps).  One bench step = the 100 steps of all 64
-    problems.  Beside it: the same problems solved one after another (each with its own
+    members stepped together by the library's batch: one persistent launch per chunk of steps
+    walking a (member, phase, tile) work list, replayed from a CUDA graph, with the tile
+    mapping per order and the chunk chosen by the autotuner (or the branch graph, if the tuner
+    measures it faster).  One bench step = the 100 steps of all 64 problems.  Beside it: the same problems solved one after another (each with its own
     graph), and every member's FP32 state against its FP64 GPU solve."""
     import torch
     import __graft_entry__
@@ -689,6 +691,7 @@ def run_batch(args):
         return a.elapsed_time(b)
 
     chunk_tune = autotune.choose_chunk(bt, solvers, u0s, steps, candidates=(5, 10, 25, 50, 100))
+    tile_tune = autotune.choose_tiles(bt, solvers, u0s, steps)
     for _ in range(args.warmup):
         one(True)
         one(False)
@@ -712,6 +715,8 @@ def run_batch(args):
         a32 = s.get_state_host().astype(np.float64)
         errs.append(float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64)))
     line = {"metric": "batched uneven solves, aggregate GDOF/s", "value": units / (ms_b / 1e3) / 1e9,
+            "batch_form": "one persistent launch per chunk of steps (work list over members, phases, tiles)"
+                          if bt.mode == rdg.BATCH_PERSISTENT else "CUDA graph of per-member branches",
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 periodic heat problems (seed 2), side 8..256, N 1..6, D log-uniform "
@@ -728,7 +733,10 @@ def run_batch(args):
                          "precision_by_order_and_size_class": sorted(
                              {(int(w.N), autotune.size_class(w.K), "fp32" if c["precision"] == rdg.FP32 else "fp32_3xtf32",
                                json.dumps(c["ms"])) for w, c in zip(probs, choices)}),
-                         "graph_chunk_ms": chunk_tune["ms"]}}
+                         "graph_chunk_ms": chunk_tune["ms"],
+                         "batch_form": tile_tune["mode"],
+                         "edges_per_thread_by_order": tile_tune["edges_per_thread"],
+                         "tile_and_form_ms": tile_tune["ms"]}}
     print(json.dumps(line), flush=True)
     bt.close()
     for s in solvers:

@@ -329,8 +329,38 @@ int rdg_batch_size(const rdg_batch* b, int* n);
  * (captured on first use after the membership changed) and the remainder as direct
  * launches on the branch streams.  Each member continues from its own time. */
 int rdg_batch_step(rdg_batch* b, int64_t nsteps);
-/* Wait for the batch stream, then check every member as rdg_synchronize does. */
+/* Wait for the batch stream, then check every member as rdg_synchronize does.  Returns
+ * RDG_ETIMEOUT if a dependency wait of the persistent form gave up (the members' states are
+ * then undefined; the batch's error word is cleared). */
 int rdg_batch_synchronize(rdg_batch* b);
+
+/* Form of a batch step.  RDG_BATCH_GRAPH: the members' own stage launches as parallel
+ * branches of one CUDA graph.  RDG_BATCH_PERSISTENT: one persistent launch per chunk of steps
+ * for all members (captured in the CUDA graph like the branches): blocks take work items
+ * (member, stage, part, tile) from a ticket counter in stage order; part A of a stage (edge
+ * fluxes, volume terms) starts once the member's previous stage is done, part B (surface
+ * terms and stage update per element) once the member's part A is done; every wait is
+ * bounded (see rdg_batch_set_wait_limit).  It needs every member FP32 with stored operators and the
+ * SSP-RK3 integrator (order 6 then forms its volume term on the CUDA cores).  RDG_BATCH_AUTO
+ * (the default): persistent when every member fits, else the graph.  The persistent form
+ * takes each member's set-up (forcing, dt, tiles) when the membership last changed.
+ * Errors: RDG_EINVAL (unknown mode, or RDG_BATCH_PERSISTENT with a member that does not fit). */
+enum { RDG_BATCH_AUTO = 0, RDG_BATCH_GRAPH = 1, RDG_BATCH_PERSISTENT = 2 };
+int rdg_batch_set_mode(rdg_batch* b, int mode);
+/* The form the next step uses (RDG_BATCH_GRAPH or RDG_BATCH_PERSISTENT) into *mode. */
+int rdg_batch_get_mode(const rdg_batch* b, int* mode);
+/* Tile mapping of the persistent form for members of order N: edges_per_thread (1 or 2)
+ * edges per thread of an edge work item (128 or 256 edges per item); element items are 128
+ * elements.  Chosen per order by the autotuner.  Errors: RDG_EINVAL. */
+int rdg_batch_set_tiles(rdg_batch* b, int N, int edges_per_thread);
+/* Bound on every dependency wait of the persistent kernel (default 1 s; (0, 60]): a wait that
+ * runs out records the timeout, and the launch ends without finishing its work. */
+int rdg_batch_set_wait_limit(rdg_batch* b, double seconds);
+/* Test hook for the bounded waits: the persistent kernel never releases stage `phase`
+ * (3 x step + stage within a launch) of member `member` (index in the order of
+ * rdg_batch_add), so that stage's items wait until the wait limit and the step reports
+ * RDG_ETIMEOUT.  member = -1 removes the hold. */
+int rdg_batch_hold_phase(rdg_batch* b, int member, int64_t phase);
 
 #ifdef __cplusplus
 }

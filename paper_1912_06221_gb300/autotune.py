@@ -5,8 +5,10 @@ operators (RDG_FP32, an HBM-bound GEMV) and the GEMM form on the tensor cores
 (RDG_FP32_3XTF32, N <= 5).  Which is faster depends on the order and the problem size, so
 the tuner times both on the caller's own problem (a few replayed stages after a warm-up) and
 caches the winner per (device, N, size class).  The graph chunk of a batch (steps per
-replayed graph) is tuned the same way on the batch itself.  All timing is CUDA events on
-the solver's stream; nothing here computes the method.
+replayed graph) is tuned the same way on the batch itself, and so is the persistent batch
+launch's tile mapping per order (edges per thread of an edge work item) and the batch form
+(persistent launch or branch graph).  All timing is CUDA events on the solver's or batch's
+stream; nothing here computes the method.
 """
 from __future__ import annotations
 
@@ -87,3 +89,49 @@ def choose_chunk(batch, members: List, u0s: List, steps: int, candidates: Iterab
     best = min(times, key=times.get)
     batch.set_chunk(best)
     return {"chunk": best, "ms": times}
+
+
+def _time_batch(torch, batch, members, u0s, steps):
+    for s, u in zip(members, u0s):
+        s.set_state(u)
+    batch.step(steps)                      # capture and warm up
+    torch.cuda.synchronize()
+    for s, u in zip(members, u0s):
+        s.set_state(u)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(batch.stream)
+    batch.step(steps)
+    b.record(batch.stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def choose_tiles(batch, members: List, u0s: List, steps: int) -> dict:
+    """Per-order tile mapping of the persistent batch launch: for every order present, one
+    or two edges per thread of an edge work item, chosen one order at a time (the others kept
+    at their best so far) by timing the batch itself.  Then the batch form (the persistent
+    launch or the branch graph) by timing both.  The batch is left with the best choices;
+    returns them and every time."""
+    import torch
+    orders = sorted({s.N for s in members})
+    times = {}
+    best = {}
+    if batch.mode != rdg.BATCH_PERSISTENT:
+        return {"mode": "graph", "edges_per_thread": {}, "ms": {}}
+    for N in orders:
+        tN = {}
+        for e in (1, 2):
+            batch.set_tiles(N, e)
+            tN[e] = _time_batch(torch, batch, members, u0s, steps)
+        best[N] = min(tN, key=tN.get)
+        batch.set_tiles(N, best[N])
+        times["N%d" % N] = tN
+    # the last order's best time was taken with every order at its best
+    t_pers = times["N%d" % orders[-1]][best[orders[-1]]]
+    batch.set_mode(rdg.BATCH_GRAPH)
+    t_graph = _time_batch(torch, batch, members, u0s, steps)
+    mode = "persistent" if t_pers <= t_graph else "graph"
+    batch.set_mode(rdg.BATCH_AUTO if mode == "persistent" else rdg.BATCH_GRAPH)
+    times["persistent"] = t_pers
+    times["graph"] = t_graph
+    return {"mode": mode, "edges_per_thread": best, "ms": times}

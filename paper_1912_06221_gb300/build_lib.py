@@ -19,7 +19,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object name, extra defines): the hot-path kernels build once per order/precision
 SOURCES = [("refops.cpp", "refops", []), ("api.cpp", "api", []), ("rhs_dispatch.cpp", "rhs_dispatch", []),
            ("setup.cu", "setup", []), ("rhs_static.cu", "rhs_static", []), ("batch.cpp", "batch", []),
-           ("measure.cu", "measure", []), ("halo.cu", "halo", [])]
+           ("measure.cu", "measure", []), ("halo.cu", "halo", []),
+           ("batch_kernel.cu", "batch_kernel", [])]
 for _n in range(1, 7):
     for _t, _tag in (("float", "f"), ("double", "d")):
         SOURCES.append(("rhs_order.cu", "rhs_%s%d" % (_tag, _n),

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "batch_kernel.h"
 #include "context.h"
 
 struct rdg_batch {
@@ -34,6 +35,21 @@ struct rdg_batch {
   cudaStream_t cap = nullptr;     // private stream the graph is captured on
   cudaGraphExec_t gexec = nullptr;
   int g_chunk = 0;
+  // persistent form: one launch per chunk of steps of every member
+  int mode = RDG_BATCH_AUTO;
+  int ept[7] = {1, 1, 1, 1, 1, 1, 1};   // edges per thread of an edge tile, per order
+  double wait_s = 1.0;                  // bound on every dependency wait of the kernel
+  int hold_member = -1;                 // test hook: this member's phase hold_phase never starts
+  int64_t hold_phase = -1;
+  bool dirty = true;                    // descriptors to rebuild before the next launch
+  rdg::BMember* d_members = nullptr;
+  unsigned long long* d_ticket = nullptr;   // ticket, then one count per member
+  int* d_flags = nullptr;               // abort flag, error word
+  float* d_tabs = nullptr;
+  int nm_alloc = 0;
+  rdg::BatchArgs args{};
+  int grid = 0;
+  size_t smem = 0;
 };
 
 namespace {
@@ -68,9 +84,135 @@ void release_member(rdg_batch::Member& m) {
   if (m.branch) cudaStreamDestroy(m.branch);
 }
 
+// The persistent form applies when every member is FP32 with stored operators and SSP-RK3.
+bool persistent_fits(const rdg_batch* b) {
+  for (const auto& m : b->members) {
+    const rdg_ctx* c = m.ctx;
+    if (c->esz != 4 || c->gemm || c->integrator != RDG_INTEGRATOR_SSP_RK3) return false;
+  }
+  return !b->members.empty();
+}
+
+bool use_persistent(const rdg_batch* b) {
+  if (b->mode == RDG_BATCH_GRAPH) return false;
+  return persistent_fits(b);
+}
+
+void free_persistent(rdg_batch* b) {
+  cudaFree(b->d_members);
+  cudaFree(b->d_ticket);
+  cudaFree(b->d_flags);
+  cudaFree(b->d_tabs);
+  b->d_members = nullptr;
+  b->d_ticket = nullptr;
+  b->d_flags = nullptr;
+  b->d_tabs = nullptr;
+  b->nm_alloc = 0;
+  b->dirty = true;
+}
+
+// Descriptors, tables and counters of the persistent launch (after a membership change).
+int prepare_persistent(rdg_batch* b) {
+  if (!b->dirty) return RDG_OK;
+  free_persistent(b);
+  const int nm = (int)b->members.size();
+  std::vector<rdg::BMember> hm(nm);
+  bool orders[7] = {false, false, false, false, false, false, false};
+  int64_t off = 0, offb = 0;
+  for (int i = 0; i < nm; ++i) {
+    const rdg_ctx* c = b->members[i].ctx;
+    rdg::BMember& d = hm[i];
+    d.W = c->d_W;
+    d.k1 = c->d_k1;
+    d.k2 = c->d_k2;
+    d.f12 = c->d_f12;
+    d.u = (float*)c->d_u;
+    d.u1 = (float*)c->d_u1;
+    d.u2 = (float*)c->d_u2;
+    d.vol = (float*)c->d_vol;
+    d.fb = (float*)c->d_fb;
+    d.geo = (const float*)c->d_geo;
+    d.S = (const float*)c->d_S;
+    d.G = (const float*)c->d_G;
+    d.err = c->d_err;
+    d.ts = c->d_time;
+    d.K = c->K;
+    d.E = c->E;
+    d.B = c->B;
+    d.frc = c->frc;
+    d.dt = b->members[i].dt;
+    d.dt32 = (float)b->members[i].dt;
+    d.N = c->N;
+    d.ept = b->ept[c->N];
+    d.ntile_v = (c->K + rdg::kStageBlock - 1) / rdg::kStageBlock;
+    const int64_t per_tile = (int64_t)rdg::kStageBlock * d.ept;
+    d.ntile_e = (c->E + per_tile - 1) / per_tile;
+    d.ntile_u = d.ntile_v;
+    d.off_a = off;
+    d.off_b = offb;
+    d.hold_phase = i == b->hold_member ? b->hold_phase : -1;
+    off += d.ntile_e + d.ntile_v;
+    offb += d.ntile_u;
+    orders[c->N] = true;
+  }
+  std::vector<float> tabs;
+  int toff[7];
+  int rc = rdg::batch_tables(orders, tabs, toff);
+  if (rc != RDG_OK) return bfail(b, rc, "reference tables");
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_members, nm * sizeof(rdg::BMember))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_ticket, (2 * nm + 1) * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_flags, 2 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_tabs, std::max<size_t>(tabs.size(), 4) * sizeof(float))) != cudaSuccess) {
+    free_persistent(b);
+    return bcuda(b, e, "persistent batch buffers");
+  }
+  if ((e = cudaMemcpy(b->d_members, hm.data(), nm * sizeof(rdg::BMember), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_tabs, tabs.data(), tabs.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(b->d_flags, 0, 2 * sizeof(int))) != cudaSuccess) {
+    free_persistent(b);
+    return bcuda(b, e, "persistent batch upload");
+  }
+  rdg::BatchArgs& a = b->args;
+  a.m = b->d_members;
+  a.nm = nm;
+  a.items_a = off;
+  a.per_phase = off + offb;
+  a.ticket = b->d_ticket;
+  a.done = b->d_ticket + 1;
+  a.abort = b->d_flags;
+  a.err = b->d_flags + 1;
+  a.tabs = b->d_tabs;
+  for (int n = 0; n < 7; ++n) a.tab_off[n] = toff[n];
+  a.tab_floats = (int)tabs.size();
+  a.wait_ns = (uint64_t)(b->wait_s * 1e9);
+  b->smem = rdg::batch_smem_bytes(a.tab_floats);
+  b->grid = rdg::batch_grid(b->smem);
+  if (b->grid <= 0) {
+    free_persistent(b);
+    return bfail(b, RDG_ECUDA, "persistent batch kernel occupancy");
+  }
+  b->nm_alloc = nm;
+  b->dirty = false;
+  return RDG_OK;
+}
+
+// nsteps steps of every member in one persistent launch on `root`, then the time origins.
+int enqueue_persistent(rdg_batch* b, cudaStream_t root, int nsteps) {
+  cudaError_t e = cudaMemsetAsync(b->d_ticket, 0, (2 * b->nm_alloc + 1) * sizeof(unsigned long long), root);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flags, 0, sizeof(int), root);   // abort flag only
+  if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
+  rdg::BatchArgs a = b->args;
+  a.nphase = 3 * nsteps;
+  int rc = rdg::launch_batch_persistent(a, b->grid, b->smem, root);
+  if (rc == RDG_OK) rc = rdg::launch_batch_advance(b->d_members, b->nm_alloc, nsteps, root);
+  return rc == RDG_OK ? RDG_OK : bfail(b, rc, "kernel launch failed");
+}
+
 // Fork from `root` to every member's branch, enqueue nsteps steps per member (each reads its
 // time origin from its device time state, which the branch then advances), join on `root`.
 int enqueue_all(rdg_batch* b, cudaStream_t root, int nsteps) {
+  if (use_persistent(b)) return enqueue_persistent(b, root, nsteps);
   cudaError_t e = cudaEventRecord(b->ev_fork, root);
   if (e != cudaSuccess) return bcuda(b, e, "cudaEventRecord");
   for (auto& m : b->members) {
@@ -90,6 +232,10 @@ int enqueue_all(rdg_batch* b, cudaStream_t root, int nsteps) {
 
 int capture(rdg_batch* b, int chunk) {
   drop_graph(b);
+  if (use_persistent(b)) {
+    int rc = prepare_persistent(b);
+    if (rc != RDG_OK) return rc;
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bcuda(b, e, "cudaStreamBeginCapture");
@@ -153,6 +299,7 @@ int rdg_batch_destroy(rdg_batch* b) {
     cudaStreamSynchronize(m.branch);
     release_member(m);
   }
+  free_persistent(b);
   cudaEventDestroy(b->ev_fork);
   cudaEventDestroy(b->ev_out);
   cudaStreamDestroy(b->cap);
@@ -187,6 +334,7 @@ int rdg_batch_add(rdg_batch* b, rdg_ctx* ctx, double t0, double dt) {
   }
   b->members.push_back(m);
   drop_graph(b);
+  b->dirty = true;
   return RDG_OK;
 }
 
@@ -197,8 +345,10 @@ int rdg_batch_remove(rdg_batch* b, rdg_ctx* ctx) {
     if (b->members[i].ctx != ctx) continue;
     cudaStreamSynchronize(b->members[i].branch);
     release_member(b->members[i]);
+    cudaStreamSynchronize(b->stream);   // a persistent launch reads every member's descriptor
     b->members.erase(b->members.begin() + (ptrdiff_t)i);
     drop_graph(b);
+    b->dirty = true;
     return RDG_OK;
   }
   return bfail(b, RDG_EINVAL, "context is not in the batch");
@@ -243,6 +393,10 @@ int rdg_batch_step(rdg_batch* b, int64_t nsteps) {
       if ((e = cudaGraphLaunch(b->gexec, b->stream)) != cudaSuccess) return bcuda(b, e, "cudaGraphLaunch");
   }
   if (done < nsteps) {
+    if (use_persistent(b)) {
+      int rc = prepare_persistent(b);
+      if (rc != RDG_OK) return rc;
+    }
     int rc = enqueue_all(b, b->stream, (int)(nsteps - done));
     if (rc != RDG_OK) return rc;
   }
@@ -259,11 +413,75 @@ int rdg_batch_synchronize(rdg_batch* b) {
     DevGuard g(b->device);
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize");
+    if (b->d_flags) {
+      int fl[2] = {0, 0};
+      if ((e = cudaMemcpy(fl, b->d_flags, sizeof(fl), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return bcuda(b, e, "cudaMemcpy");
+      if (fl[1] & rdg::kErrWaitTimeout) {
+        // the launch gave up part-way: the members' states are undefined; clear the error word
+        if ((e = cudaMemset(b->d_flags, 0, 2 * sizeof(int))) != cudaSuccess) return bcuda(b, e, "cudaMemset");
+        return bfail(b, RDG_ETIMEOUT, "a dependency wait of the persistent batch kernel gave up");
+      }
+    }
   }
   for (auto& m : b->members) {
     int rc = rdg_synchronize(m.ctx);
     if (rc != RDG_OK) return bfail(b, rc, std::string("member: ") + rdg_last_error(m.ctx));
   }
+  return RDG_OK;
+}
+
+int rdg_batch_set_mode(rdg_batch* b, int mode) {
+  if (!b) return RDG_EINVAL;
+  if (mode != RDG_BATCH_AUTO && mode != RDG_BATCH_GRAPH && mode != RDG_BATCH_PERSISTENT)
+    return bfail(b, RDG_EINVAL, "mode must be RDG_BATCH_AUTO, RDG_BATCH_GRAPH or RDG_BATCH_PERSISTENT");
+  if (mode == RDG_BATCH_PERSISTENT && !b->members.empty() && !persistent_fits(b))
+    return bfail(b, RDG_EINVAL, "the persistent form needs FP32 members with stored operators and SSP-RK3");
+  DevGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->mode = mode;
+  drop_graph(b);
+  return RDG_OK;
+}
+
+int rdg_batch_get_mode(const rdg_batch* b, int* mode) {
+  if (!b || !mode) return RDG_EINVAL;
+  *mode = use_persistent(b) ? RDG_BATCH_PERSISTENT : RDG_BATCH_GRAPH;
+  return RDG_OK;
+}
+
+int rdg_batch_set_tiles(rdg_batch* b, int N, int edges_per_thread) {
+  if (!b) return RDG_EINVAL;
+  if (N < 1 || N > 6 || edges_per_thread < 1 || edges_per_thread > 2)
+    return bfail(b, RDG_EINVAL, "N must be in 1..6 and edges_per_thread 1 or 2");
+  DevGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->ept[N] = edges_per_thread;
+  b->dirty = true;
+  drop_graph(b);
+  return RDG_OK;
+}
+
+int rdg_batch_set_wait_limit(rdg_batch* b, double seconds) {
+  if (!b) return RDG_EINVAL;
+  if (!(seconds > 0) || seconds > 60) return bfail(b, RDG_EINVAL, "wait limit must be in (0, 60] seconds");
+  DevGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->wait_s = seconds;
+  b->dirty = true;
+  drop_graph(b);
+  return RDG_OK;
+}
+
+int rdg_batch_hold_phase(rdg_batch* b, int member, int64_t phase) {
+  if (!b) return RDG_EINVAL;
+  if (member < -1 || member >= (int)b->members.size()) return bfail(b, RDG_EINVAL, "no such member");
+  DevGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->hold_member = member;
+  b->hold_phase = phase;
+  b->dirty = true;
+  drop_graph(b);
   return RDG_OK;
 }
 

@@ -21,6 +21,7 @@ FP64, FP32, FP32_3XTF32 = 0, 1, 2
 TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
 IFACE_ALG2, IFACE_HARMONIC, IFACE_ALG1 = 0, 1, 2
 SSP_RK3, LSRK54 = 0, 1
+BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
 
 # symbol -> (restype, argtypes)
@@ -72,6 +73,11 @@ SIGNATURES = {
     "rdg_batch_set_chunk": (_INT, [_P, _INT]),
     "rdg_batch_step": (_INT, [_P, _I64]),
     "rdg_batch_synchronize": (_INT, [_P]),
+    "rdg_batch_set_mode": (_INT, [_P, _INT]),
+    "rdg_batch_get_mode": (_INT, [_P, ctypes.POINTER(_INT)]),
+    "rdg_batch_set_tiles": (_INT, [_P, _INT, _INT]),
+    "rdg_batch_set_wait_limit": (_INT, [_P, _D]),
+    "rdg_batch_hold_phase": (_INT, [_P, _INT, _I64]),
 }
 
 _lib = None
@@ -384,6 +390,26 @@ class Batch:
 
     def synchronize(self):
         self._call("rdg_batch_synchronize")
+
+    def set_mode(self, mode: int):
+        """BATCH_AUTO (default), BATCH_GRAPH or BATCH_PERSISTENT."""
+        self._call("rdg_batch_set_mode", int(mode))
+
+    @property
+    def mode(self) -> int:
+        m = _INT(0)
+        self._call("rdg_batch_get_mode", ctypes.byref(m))
+        return m.value
+
+    def set_tiles(self, N: int, edges_per_thread: int):
+        self._call("rdg_batch_set_tiles", int(N), int(edges_per_thread))
+
+    def set_wait_limit(self, seconds: float):
+        self._call("rdg_batch_set_wait_limit", float(seconds))
+
+    def hold_phase(self, member: int, phase: int):
+        """Test hook: phase `phase` of member `member` is never released (-1: no hold)."""
+        self._call("rdg_batch_hold_phase", int(member), int(phase))
 
     def close(self):
         if getattr(self, "b", None):
