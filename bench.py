@@ -64,6 +64,8 @@ def parse():
                    help="the circle pulse stage at every order N = 1..6, FP32 and FP64, instead")
     p.add_argument("--orders-list", default="1,2,3,4,5,6")
     p.add_argument("--orders-precisions", default="fp32,fp64")
+    p.add_argument("--hbm-read", action="store_true",
+                   help="plain streaming-read time and bandwidth at a few sizes (the size-matched HBM bound)")
     return p.parse_args()
 
 
@@ -431,6 +433,18 @@ def run_ours(args):
                             "flops_per_stage": flops_stage}
     compute_peaks = {"fp32_tflops": p32 / 1e12, "fp64_tflops": p64 / 1e12,
                      "how": "rdg_peak_fma: independent FMA chains on every SM, CUDA events, best of 4"}
+    # the size-matched bound: a plain streaming read of the stage's algorithmic bytes and of
+    # the operators alone, each a standalone launch (rdg_stream_read)
+    w_bytes = ((E + 31) // 32) * ((Nfp * (2 * Np - 1) + 1 + 3) // 4) * 32 * 16
+    t_rd_stage = rdg.stream_read_seconds(local, stage_alg)
+    t_rd_w = rdg.stream_read_seconds(local, w_bytes)
+    roof["size_matched_read"] = {"stage_alg_bytes": stage_alg, "read_us": t_rd_stage * 1e6,
+                                 "read_gbs": stage_alg / t_rd_stage / 1e9,
+                                 "operator_bytes": w_bytes, "operator_read_us": t_rd_w * 1e6,
+                                 "stage_us_in_graph": t_stage_s * 1e6,
+                                 "stage_time_over_read_time": t_stage_s / t_rd_stage,
+                                 "how": "rdg_stream_read: float4 evict-first grid-stride read, L2 flushed, "
+                                        "median of 8 standalone launches"}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_t = []
@@ -735,7 +749,7 @@ def run_batch(args):
                                json.dumps(c["ms"])) for w, c in zip(probs, choices)}),
                          "graph_chunk_ms": chunk_tune["ms"],
                          "batch_form": tile_tune["mode"],
-                         "edges_per_thread_by_order": tile_tune["edges_per_thread"],
+                         "edges_per_thread_tiles_per_item_by_order": tile_tune["edges_per_thread_tiles_per_item"],
                          "tile_and_form_ms": tile_tune["ms"]}}
     print(json.dumps(line), flush=True)
     bt.close()
@@ -879,7 +893,7 @@ def run_sweep(args):
 def run_orders(args):
     """Graph-replayed SSP-RK3 stage of the circle pulse workload (m x m x 2 triangles) at each
     order, FP32 and FP64: microseconds per stage, GDOF/s and the stage's algorithmic HBM
-    bytes (stored operators, element rows, face fluxes) per second."""
+    bytes (stored operators, state in and out, coefficients and ids) per second."""
     import torch
     import paper_1912_06221_gb300 as rdg
     from synth import circle_pulse
@@ -915,10 +929,14 @@ def run_orders(args):
             # ids, face fluxes, stage input, volume term, element coefficients) and element pass
             # (volume term, stage input, step start in two of three stages, output, ids, 1/J,
             # face fluxes)
-            alg = (E * ((Nfp * (2 * Np - 1) + 1) * esz + 8 + Nfp * esz) + 2 * K * Np * esz + K * 5 * esz
+            # the survey's algorithmic bytes per element (stored operators, state in and out,
+            # coefficients, ids); the two kernels' own bytes (intermediates included) beside
+            alg = alg_bytes_per_element(N, esz) * K
+            own = (E * ((Nfp * (2 * Np - 1) + 1) * esz + 8 + Nfp * esz) + 2 * K * Np * esz + K * 5 * esz
                    + int(K * ((3 + 2.0 / 3.0) * Np * esz + 12 + esz) + E * Nfp * esz))
             rows.append({"N": N, "precision": name, "stage_us": us, "gdofs": s.K * Np / (us * 1e-6) / 1e9,
-                         "operator_mb": w_bytes / 1e6, "alg_mb": alg / 1e6, "alg_gbs": alg / (us * 1e-6) / 1e9})
+                         "operator_mb": w_bytes / 1e6, "alg_mb": alg / 1e6, "alg_gbs": alg / (us * 1e-6) / 1e9,
+                         "kernels_own_mb": own / 1e6})
             s.synchronize()
             s.close()
     clocks = clk.stop()
@@ -937,6 +955,23 @@ def run_orders(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hbm_read(args):
+    """Plain streaming reads (rdg_stream_read) of 115 MiB, 150 MiB and 1 GiB, event-timed: how
+    the reachable read bandwidth of one standalone launch depends on its size."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06221_gb300 as rdg
+    rows = []
+    for mib in (115, 150, 1024):
+        t = rdg.stream_read_seconds(0, mib << 20)
+        rows.append({"bytes": mib << 20, "us": t * 1e6, "gbs": (mib << 20) / t / 1e9})
+    (b1, t1), (b2, t2) = [(r["bytes"], r["us"]) for r in rows[1:]]
+    slope = (t2 - t1) / (b2 - b1)
+    line = {"metric": "streaming read time by size", "unit": "us", "rows": rows,
+            "asymptotic_gbs": 1e-3 / slope, "fixed_us": t1 - slope * b1, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -951,5 +986,7 @@ if __name__ == "__main__":
         run_sweep(a)
     elif a.orders:
         run_orders(a)
+    elif a.hbm_read:
+        run_hbm_read(a)
     else:
         run_ours(a)

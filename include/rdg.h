@@ -144,6 +144,20 @@ int rdg_operator_setup(rdg_ctx* ctx, int N, const double* D_elem, double vx, dou
 int rdg_operator_setup_aniso(rdg_ctx* ctx, int N, const double* Dx, const double* Dy, double vx, double vy,
                              int precision, int interface_rule);
 
+/* rdg_operator_setup for a spatially varying D given at the nodes (Sec. 3: D a function of
+ * space in Eq. NDG_diffusion_once_matrixForm_reference_general): D_nodal[nt][Np] (> 0) in the
+ * element's node order.  The volume flux is the nodal product v u - D grad u; the edge
+ * diffusion is, for RDG_IFACE_ALG2, D~ reconstructed on the diagonal from both elements'
+ * nodal D (Algorithm 2), for RDG_IFACE_ALG1 each element's D evaluated at its sub-triangle's
+ * nodes and multiplied into that sub-triangle's gradient before the second reconstruction
+ * (Algorithm 1), for RDG_IFACE_HARMONIC the harmonic mean of the two elements' D at each face
+ * node; a Dirichlet ghost's D is its element's D at the point reflections.  Stored operators
+ * only (with RDG_FP32_3XTF32 the RDG_FP32 path runs; order 6 in FP32 forms the volume term on
+ * the CUDA cores); not for rdg_rhs_eval_static or the persistent batch form.  Device memory:
+ * rdg_query_bytes plus nt x Np values.  Errors: as rdg_operator_setup. */
+int rdg_operator_setup_nodal(rdg_ctx* ctx, int N, const double* D_nodal, double vx, double vy, int precision,
+                             int interface_rule);
+
 /* Separable forcing (after rdg_operator_setup).  Source s(x,t) = sum_m S_m(x) tau_m(t) with
  * S given as nodal values S[nsrc][nt][Np] (host, double), tau_m = 1, cos(w t) or sin(w t)
  * per src_kind[m], src_omega[m].  Dirichlet ghost data g(x,t) = sum_m G_m(x) tau_m(t) with
@@ -264,7 +278,12 @@ int rdg_query_bytes(int N, int64_t nt, int64_t n_edges, int64_t n_boundary, int 
  * sum_rho kappa_rho sum_m psi_m(alpha_k, beta_k) X[k][m][i][rho][l] (Sec. 4.4-4.5, Eq.
  * totalProjection: the projection is polynomial in the apex coordinates); 7 the node
  * permutations [3][Np] (rotated node i of face f is node perm[f][i]); 8 the rotated-order
- * indices of the shared face's nodes [Nfp].  out must hold the stated number of doubles. */
+ * indices of the shared face's nodes [Nfp]; for a nodal D (rdg_operator_setup_nodal):
+ * 9 RVV[2 sides j][Nfp][Np] = Phi_diag A+_j Vinv, the reconstruction on the diagonal of side
+ * j's modal data, brought to nodal input; 10 GR[2 j][2 k][Np][Np] = Dr V A_j A+_k Vinv and
+ * 11 GS (Ds in place of Dr): Algorithm 1's edge gradient with D at the sub-triangle nodes is
+ * sum_j s_j RVV[j] diag(D_p^j) (kappa_R GR[j][k] + kappa_S GS[j][k]) u_k,rot, s_1 = 1,
+ * s_2 = -1 (Sec. 3, Algorithm 1; Sec. 4.5).  out must hold the stated number of doubles. */
 int rdg_reference_operator(int N, int which, double* out);
 
 /* Per-edge flux operators in FP64 as built on the GPU: W[n_edges][Nfp][2Np] (host,
@@ -293,6 +312,15 @@ int rdg_error_norms(rdg_ctx* ctx, const void* u_dev, const double* ue_q_dev, dou
  * warm-up launches, at whatever clocks the GPU runs (nothing is locked or changed).  The
  * compute side of the right-hand side's roofline.  Errors: RDG_EINVAL, RDG_ENOMEM, RDG_ECUDA. */
 int rdg_peak_fma(int device, int precision, double* flops_per_second);
+
+/* Time of a plain streaming read of `bytes` (16..64 GiB) from device memory on `device`:
+ * 16-byte evict-first loads, grid-stride over 8 blocks per SM, a 512 MiB buffer written
+ * between timed reads (larger than L2), median of eight launches after two warm-up ones,
+ * CUDA events.  The size-matched bound of an HBM-streaming kernel: a standalone launch pays a
+ * fixed ramp-up and tail, so a read of 100 MB reaches well under the copy peak measured on
+ * gigabytes.  Allocates bytes + 512 MiB and frees them.  Errors: RDG_EINVAL, RDG_ENOMEM,
+ * RDG_ECUDA. */
+int rdg_stream_read(int device, int64_t bytes, double* seconds);
 
 /* ---- Batched stepping of independent problems ------------------------------------------
  * Many independent solves (different meshes, orders N = 1..6, precisions, dt) advanced
@@ -350,9 +378,11 @@ int rdg_batch_set_mode(rdg_batch* b, int mode);
 /* The form the next step uses (RDG_BATCH_GRAPH or RDG_BATCH_PERSISTENT) into *mode. */
 int rdg_batch_get_mode(const rdg_batch* b, int* mode);
 /* Tile mapping of the persistent form for members of order N: edges_per_thread (1 or 2)
- * edges per thread of an edge work item (128 or 256 edges per item); element items are 128
- * elements.  Chosen per order by the autotuner.  Errors: RDG_EINVAL. */
-int rdg_batch_set_tiles(rdg_batch* b, int N, int edges_per_thread);
+ * edges per thread of an edge tile (128 or 256 edges per tile; element tiles are 128
+ * elements) and tiles_per_item (1, 2 or 4) consecutive tiles per work item, which amortises
+ * an item's dependency check over more work.  Chosen per order by the autotuner.  Errors:
+ * RDG_EINVAL. */
+int rdg_batch_set_tiles(rdg_batch* b, int N, int edges_per_thread, int tiles_per_item);
 /* Bound on every dependency wait of the persistent kernel (default 1 s; (0, 60]): a wait that
  * runs out records the timeout, and the launch ends without finishing its work. */
 int rdg_batch_set_wait_limit(rdg_batch* b, double seconds);

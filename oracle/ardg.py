@@ -166,12 +166,19 @@ class EdgeOps:
         RDG - least-squares reconstruction of each component from the two sub-triangles'
         modal data, evaluated at the diagonal nodes; then n1 . (.).
 
-        D1, D2 are [E] (isotropic) or [E, 2] (the diagonal tensor (Dx, Dy) of Eq.
-        NDG_diffusion_once_matrixForm_reference_general: component x of the product uses Dx)."""
+        D1, D2 are [E] (isotropic), [E, 2] (the diagonal tensor (Dx, Dy) of Eq.
+        NDG_diffusion_once_matrixForm_reference_general: component x of the product uses Dx),
+        or [E, Np] (nodal values of a spatially varying D on each side's element, in the
+        element's own node order): then D_p^k = V_pk D^k is the element's D evaluated at the
+        nodes of the sub-triangle, V (P_k D^k) with the projection P_k of Eq. totalProjection."""
         ops = self.mesh.ops
         Rx, Ry, Sx, Sy = self.Rx.T
         Phi = ops.phi(ops.diag_R, ops.diag_S)
         out = np.zeros((c.shape[0], ops.Nfp))
+        nodal = np.asarray(D1).ndim == 2 and np.asarray(D1).shape[1] == ops.Np
+        if nodal:   # D_p^k at the sub-triangle nodes
+            D1 = np.einsum("ij,ejk,ek->ei", ops.V, self.P1, np.asarray(D1))
+            D2 = np.einsum("ij,ejk,ek->ei", ops.V, self.P2, np.asarray(D2))
         for comp in range(2):
             dRphys = Rx if comp == 0 else Ry     # d/dx = R_x d/dR + S_x d/dS (y likewise)
             dSphys = Sx if comp == 0 else Sy
@@ -183,8 +190,11 @@ class EdgeOps:
                 ds = nod @ ops.Ds.T
                 g = sgn * (dRphys[:, None] * dr + dSphys[:, None] * ds)
                 Dc = np.asarray(Dk)
-                Dc = Dc[:, comp] if Dc.ndim == 2 else Dc
-                w = Dc[:, None] * g                 # Product with D_p^k (component comp)
+                if nodal:
+                    w = Dc * g                      # Product with D_p^k at the nodes
+                else:
+                    Dc = Dc[:, comp] if Dc.ndim == 2 else Dc
+                    w = Dc[:, None] * g             # Product with D_p^k (component comp)
                 modal.append(w @ ops.Vinv.T)        # modal data of the component on Omega'_k
             cc = np.concatenate(modal, axis=1) @ ops.Apinv.T   # RDG of the component
             out += self.n1[:, comp:comp + 1] * (cc @ Phi.T)

@@ -52,9 +52,13 @@ class Problem:
     """A mesh plus coefficients: D per element, constant velocity v, optional separable
     source and Dirichlet ghost data (lists of (nodal profile, kind, omega)).
 
-    D_elem: [K] for isotropic diffusion, or [K, 2] for the diagonal tensor D = (Dx, Dy) of Eq.
+    D_elem: [K] for isotropic diffusion, [K, 2] for the diagonal tensor D = (Dx, Dy) of Eq.
     NDG_diffusion_once_matrixForm_reference_general (the volume flux is (Dx u_x, Dy u_y); the
-    interface rules below act on each component).
+    interface rules below act on each component), or [K, Np] for a spatially varying D given
+    at the nodes (the volume flux is the nodal product D grad u; Algorithm 2 reconstructs D~
+    from both elements' nodal D, the harmonic rule takes the harmonic mean of the two traces,
+    Algorithm 1 evaluates each element's D at its sub-triangle's nodes).  A Dirichlet ghost's
+    nodal D is its element's D at the reflected points.
 
     interface: how the edge diffusion coefficient D~ is formed for element-wise D.
       "alg1"      the paper's Algorithm 1: the edge flux is n . RDG(D_p^1 grad u~^1,
@@ -79,26 +83,55 @@ class Problem:
         self.k2 = np.array([e[2] for e in m.edges])
         self.f2 = np.array([e[3] for e in m.edges])
         self.interior = self.k2 >= 0
-        self.aniso = self.D.ndim == 2
+        ops = m.ops
+        self.nodal = self.D.ndim == 2 and self.D.shape[1] == ops.Np
+        self.aniso = self.D.ndim == 2 and not self.nodal
         if self.aniso and self.D.shape[1] != 2:
-            raise ValueError("D_elem must be [K] or [K, 2]")
-        inner = self.interior[:, None] if self.aniso else self.interior
+            raise ValueError("D_elem must be [K], [K, 2] or [K, Np]")
+        self.bnd = np.flatnonzero(~self.interior)
+        self.ghost_xy = [m.ghost_nodes(e) for e in self.bnd]
+        inner = self.interior[:, None] if self.D.ndim == 2 else self.interior
         D2 = np.where(inner, self.D[np.maximum(self.k2, 0)], self.D[self.k1])
+        if self.nodal and self.bnd.size:
+            D2[self.bnd] = self._ghost_D()
         self.interface = interface
         self.D1e, self.D2e = self.D[self.k1], D2
         comps = [(self.D1e[:, c], D2[:, c]) for c in range(2)] if self.aniso else [(self.D1e, D2)]
         if interface == "alg1":
             self.Dt = None
+        elif interface == "alg2" and self.nodal:
+            self.Dt = self.eops.reconstructed_values(self.eops.reconstruct(self.D1e, D2))
         elif interface == "alg2":
             self.Dt = [self.eops.reconstruct_D(a, b) for a, b in comps]
+        elif interface == "harmonic" and self.nodal:
+            t1 = np.take_along_axis(self.D1e, np.stack([ops.Fmask[f] for f in self.f1]), axis=1)
+            f2i = np.where(self.interior, self.f2, 1)
+            t2 = np.take_along_axis(D2, np.stack([ops.Fmask[f][::-1] for f in f2i]), axis=1)
+            self.Dt = 2 * t1 * t2 / (t1 + t2)
         elif interface == "harmonic":
             self.Dt = [np.repeat((2 * a * b / (a + b))[:, None], mesh.ops.Nfp, axis=1) for a, b in comps]
         else:
             raise ValueError(interface)
-        if not self.aniso and self.Dt is not None:
+        if not self.aniso and not self.nodal and self.Dt is not None:
             self.Dt = self.Dt[0]
-        self.bnd = np.flatnonzero(~self.interior)
-        self.ghost_xy = [m.ghost_nodes(e) for e in self.bnd]
+
+    def _ghost_D(self):
+        """Nodal D of every ghost: its element's D at the point reflections of the ghost's nodes
+        (the ghost is the element reflected about the edge midpoint)."""
+        m = self.mesh
+        ops = m.ops
+        out = np.zeros((self.bnd.size, ops.Np))
+        for i, e in enumerate(self.bnd):
+            k1, f1 = self.k1[e], self.f1[e]
+            a, b = FACE_VERTS[f1]
+            c2 = m.V[k1, a] + m.V[k1, b]
+            gx, gy = self.ghost_xy[i]
+            px, py = c2[0] - gx, c2[1] - gy
+            v1, v2, v3 = m.V[k1]
+            Amat = np.column_stack([(v2 - v1) / 2, (v3 - v1) / 2])
+            rs = np.linalg.solve(Amat, np.stack([px - (v2[0] + v3[0]) / 2, py - (v2[1] + v3[1]) / 2]))
+            out[i] = psi(ops.N, rs[0], rs[1]) @ (ops.Vinv @ self.D[k1])
+        return out
 
     def ghost_values(self, t):
         Np = self.mesh.ops.Np
@@ -135,8 +168,11 @@ class Problem:
     def rhs(self, u, t=0.0):
         m = self.mesh
         ops = m.ops
-        Dx = (self.D[:, 0] if self.aniso else self.D)[:, None]
-        Dy = (self.D[:, 1] if self.aniso else self.D)[:, None]
+        if self.nodal:
+            Dx = Dy = self.D
+        else:
+            Dx = (self.D[:, 0] if self.aniso else self.D)[:, None]
+            Dy = (self.D[:, 1] if self.aniso else self.D)[:, None]
         ur = u @ ops.Dr.T
         us = u @ ops.Ds.T
         ux = m.rx[:, None] * ur + m.sx[:, None] * us

@@ -108,8 +108,8 @@ def _time_batch(torch, batch, members, u0s, steps):
 
 def choose_tiles(batch, members: List, u0s: List, steps: int) -> dict:
     """Per-order tile mapping of the persistent batch launch: for every order present, one
-    or two edges per thread of an edge work item, chosen one order at a time (the others kept
-    at their best so far) by timing the batch itself.  Then the batch form (the persistent
+    or two edges per thread of an edge tile and one, two or four tiles per work item, chosen
+    one order at a time (the others kept at their best so far) by timing the batch itself.  Then the batch form (the persistent
     launch or the branch graph) by timing both.  The batch is left with the best choices;
     returns them and every time."""
     import torch
@@ -117,21 +117,25 @@ def choose_tiles(batch, members: List, u0s: List, steps: int) -> dict:
     times = {}
     best = {}
     if batch.mode != rdg.BATCH_PERSISTENT:
-        return {"mode": "graph", "edges_per_thread": {}, "ms": {}}
+        return {"mode": "graph", "edges_per_thread_tiles_per_item": {}, "ms": {}}
     for N in orders:
         tN = {}
-        for e in (1, 2):
-            batch.set_tiles(N, e)
-            tN[e] = _time_batch(torch, batch, members, u0s, steps)
+        for e in (1, 2):                       # edges per thread, one tile per item
+            batch.set_tiles(N, e, 1)
+            tN[(e, 1)] = _time_batch(torch, batch, members, u0s, steps)
+        e = min((1, 2), key=lambda x: tN[(x, 1)])
+        for tpi in (2, 4):                     # then tiles per item
+            batch.set_tiles(N, e, tpi)
+            tN[(e, tpi)] = _time_batch(torch, batch, members, u0s, steps)
         best[N] = min(tN, key=tN.get)
-        batch.set_tiles(N, best[N])
-        times["N%d" % N] = tN
+        batch.set_tiles(N, *best[N])
+        times["N%d" % N] = {"%d edges/thread, %d tiles/item" % k: v for k, v in tN.items()}
     # the last order's best time was taken with every order at its best
-    t_pers = times["N%d" % orders[-1]][best[orders[-1]]]
+    t_pers = min(times["N%d" % orders[-1]].values())
     batch.set_mode(rdg.BATCH_GRAPH)
     t_graph = _time_batch(torch, batch, members, u0s, steps)
     mode = "persistent" if t_pers <= t_graph else "graph"
     batch.set_mode(rdg.BATCH_AUTO if mode == "persistent" else rdg.BATCH_GRAPH)
     times["persistent"] = t_pers
     times["graph"] = t_graph
-    return {"mode": mode, "edges_per_thread": best, "ms": times}
+    return {"mode": mode, "edges_per_thread_tiles_per_item": {N: list(v) for N, v in best.items()}, "ms": times}

@@ -71,6 +71,7 @@ void free_ops(rdg_ctx* ctx) {
   dfree(ctx->d_vol, s);
   dfree(ctx->d_fb, s);
   dfree(ctx->d_f12, s);
+  dfree(ctx->d_Dn, s);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   ctx->gexec = nullptr;
   ctx->ops_ok = false;
@@ -450,7 +451,17 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
   }
   std::vector<double> refs = pack_setup_refs(*o);
   double *d_xy = nullptr, *d_sh = nullptr, *d_D = nullptr, *d_Dy = nullptr, *d_refs = nullptr;
+  double *d_Dn64 = nullptr, *d_nref = nullptr;
   const bool aniso = !ctx->Dy.empty();
+  const bool nodal = !ctx->Dn.empty();
+  std::vector<double> nref;
+  if (nodal) {   // RVV [2][Nfp][Np], GR [2][2][Np][Np], GS [2][2][Np][Np]
+    for (int j = 0; j < 2; ++j) nref.insert(nref.end(), o->RVV[j].begin(), o->RVV[j].end());
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k) nref.insert(nref.end(), o->GR[j][k].begin(), o->GR[j][k].end());
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k) nref.insert(nref.end(), o->GS[j][k].begin(), o->GS[j][k].end());
+  }
   int32_t *d_i = nullptr;
   int rc = RDG_OK;
   cudaError_t e;
@@ -460,6 +471,8 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
     dfree(d_sh, s);
     dfree(d_D, s);
     dfree(d_Dy, s);
+    dfree(d_Dn64, s);
+    dfree(d_nref, s);
     dfree(d_refs, s);
     dfree(d_i, s);
     cudaStreamSynchronize(s);
@@ -468,6 +481,8 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
       (e = dalloc(&d_sh, 2 * E * sizeof(double), s)) != cudaSuccess ||
       (e = dalloc(&d_D, K * sizeof(double), s)) != cudaSuccess ||
       (aniso && (e = dalloc(&d_Dy, K * sizeof(double), s)) != cudaSuccess) ||
+      (nodal && (e = dalloc(&d_Dn64, ctx->Dn.size() * sizeof(double), s)) != cudaSuccess) ||
+      (nodal && (e = dalloc(&d_nref, nref.size() * sizeof(double), s)) != cudaSuccess) ||
       (e = dalloc(&d_refs, refs.size() * sizeof(double), s)) != cudaSuccess ||
       (e = dalloc(&d_i, 4 * E * sizeof(int32_t), s)) != cudaSuccess) {
     cleanup();
@@ -477,6 +492,10 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
       (e = cudaMemcpyAsync(d_sh, sh.data(), 2 * E * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_D, ctx->Dk.data(), K * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (aniso && (e = cudaMemcpyAsync(d_Dy, ctx->Dy.data(), K * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+                    cudaSuccess) ||
+      (nodal && (e = cudaMemcpyAsync(d_Dn64, ctx->Dn.data(), ctx->Dn.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                     s)) != cudaSuccess) ||
+      (nodal && (e = cudaMemcpyAsync(d_nref, nref.data(), nref.size() * sizeof(double), cudaMemcpyHostToDevice, s)) !=
                     cudaSuccess) ||
       (e = cudaMemcpyAsync(d_refs, refs.data(), refs.size() * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_i, k1.data(), E * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -492,11 +511,11 @@ static int build_edge_ops(rdg_ctx* ctx, const RefOps* o, void* W_tiled, int esz,
       return cuda_fail(ctx, e, "W clear");
     }
   }
-  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_Dy, d_refs, E, ctx->vx, ctx->vy,
-                 ctx->iface, (int64_t)refs.size()};
+  EdgeSetupIn in{d_xy, d_i, d_i + E, d_i + 2 * E, d_i + 3 * E, d_sh, d_D, d_Dy, d_Dn64, d_nref, d_refs, E, ctx->vx,
+                 ctx->vy, ctx->iface, (int64_t)refs.size()};
   rc = setup_edges(ctx->N, in, W_tiled, esz, W_dense, P_tiled, s);
   if (rc == RDG_OK && ctx->d_geo && !W_dense)
-    rc = setup_elements(K, d_xy, d_D, d_Dy, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
+    rc = setup_elements(K, d_xy, nodal ? nullptr : d_D, d_Dy, ctx->vx, ctx->vy, ctx->d_geo, esz, s);
   e = cudaStreamSynchronize(s);
   cleanup();
   if (rc != RDG_OK) return fail(ctx, rc, "setup kernel launch failed");
@@ -511,7 +530,7 @@ extern "C" {
 // Operator set-up; Dy (may be null) is the y diffusion of a diagonal tensor (D_elem then
 // holds the x diffusion), which needs the stored operators.
 static int operator_setup_impl(rdg_ctx* ctx, int N, const double* D_elem, const double* Dy, double vx, double vy,
-                               int precision, int interface_rule) {
+                               int precision, int interface_rule, const double* Dn = nullptr) {
   if (!ctx) return RDG_EINVAL;
   if (!ctx->mesh_ok) return fail(ctx, RDG_ESTATE, "rdg_mesh_upload must come first");
   if (N < 1 || N > kMaxN) return fail(ctx, RDG_EINVAL, "order N must be in 1..6");
@@ -532,13 +551,16 @@ static int operator_setup_impl(rdg_ctx* ctx, int N, const double* D_elem, const 
   ctx->N = N;
   ctx->prec = precision;
   ctx->esz = precision == RDG_FP64 ? 8 : 4;
-  ctx->gemm = uses_gemm(N, precision, interface_rule) && !Dy;   // the GEMM form folds one isotropic D~
+  // the GEMM form folds one isotropic element-wise D~
+  ctx->gemm = uses_gemm(N, precision, interface_rule) && !Dy && !Dn;
   ctx->vx = vx;
   ctx->vy = vy;
   ctx->iface = interface_rule;
   ctx->Dk.assign(D_elem, D_elem + ctx->K);
   if (Dy) ctx->Dy.assign(Dy, Dy + ctx->K);
   else ctx->Dy.clear();
+  if (Dn) ctx->Dn.assign(Dn, Dn + ctx->K * np_of(N));
+  else ctx->Dn.clear();
   const int64_t K = ctx->K, E = ctx->E, Np = o->Np, Nfp = o->Nfp, esz = ctx->esz;
   const int64_t stb = K * Np * esz;
   CK(dalloc(&ctx->d_W, ctx->gemm ? edge_data_bytes(N, E, precision) : w_bytes(N, E, (int)esz), ctx->stream));
@@ -553,6 +575,17 @@ static int operator_setup_impl(rdg_ctx* ctx, int N, const double* D_elem, const 
   CK(dalloc(&ctx->d_vol, stb, ctx->stream));
   CK(dalloc(&ctx->d_fb, K * 3 * Nfp * esz, ctx->stream));
   CK(dalloc(&ctx->d_f12, E * 4, ctx->stream));
+  if (Dn) {   // the volume term's nodal D, in the context's precision
+    CK(dalloc(&ctx->d_Dn, K * Np * esz, ctx->stream));
+    if (esz == 8) {
+      CK(cudaMemcpyAsync(ctx->d_Dn, Dn, K * Np * 8, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      std::vector<float> f(Dn, Dn + K * Np);
+      CK(cudaMemcpyAsync(ctx->d_Dn, f.data(), K * Np * 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+  }
   std::vector<int32_t> k1(E), k2(E), f12(E);
   for (int64_t e = 0; e < E; ++e) {
     k1[e] = ctx->edges[e].k1;
@@ -585,6 +618,24 @@ int rdg_operator_setup_aniso(rdg_ctx* ctx, int N, const double* Dx, const double
                              int precision, int interface_rule) {
   if (ctx && !Dy) return fail(ctx, RDG_EINVAL, "Dy is NULL");
   return operator_setup_impl(ctx, N, Dx, Dy, vx, vy, precision, interface_rule);
+}
+
+int rdg_operator_setup_nodal(rdg_ctx* ctx, int N, const double* D_nodal, double vx, double vy, int precision,
+                             int interface_rule) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->mesh_ok) return fail(ctx, RDG_ESTATE, "rdg_mesh_upload must come first");
+  if (!D_nodal) return fail(ctx, RDG_EINVAL, "D_nodal is NULL");
+  if (N < 1 || N > kMaxN) return fail(ctx, RDG_EINVAL, "order N must be in 1..6");
+  const int64_t Np = np_of(N);
+  std::vector<double> mean(ctx->K, 0.0);   // per element, only to keep every kernel argument defined
+  for (int64_t k = 0; k < ctx->K; ++k) {
+    for (int64_t j = 0; j < Np; ++j) {
+      const double d = D_nodal[k * Np + j];
+      if (!(d > 0) || !std::isfinite(d)) return fail(ctx, RDG_EINVAL, "D must be positive and finite");
+      mean[k] += d / Np;
+    }
+  }
+  return operator_setup_impl(ctx, N, mean.data(), nullptr, vx, vy, precision, interface_rule, D_nodal);
 }
 
 int rdg_get_edge_operators(rdg_ctx* ctx, double* W, int32_t* ids) {
@@ -786,7 +837,7 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
                   void* out2 = nullptr, T rka = T(0), T rkb = T(0)) {
   EdgeArgs<T> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const T*)us, (T*)ctx->d_flux, (const T*)ctx->d_G,
                  ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, (T*)ctx->d_vol,
-                 (const T*)ctx->d_geo, ctx->d_f12, (T*)ctx->d_fb, keep_tiles(ctx)};
+                 (const T*)ctx->d_geo, ctx->d_f12, (T*)ctx->d_fb, keep_tiles(ctx), (const T*)ctx->d_Dn};
   ElemArgs<T> la{(const T*)us, (const T*)un, (T*)out, (const T*)ctx->d_flux, ctx->d_eref, (const T*)ctx->d_geo,
                  (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta, ctx->d_err, ctx->E, (const T*)ctx->d_vol,
                  (const T*)ctx->d_fb, (T*)out2, rka, rkb};
@@ -799,7 +850,7 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
   if (prof) cudaEventRecord(ev[0], st);
   if constexpr (sizeof(T) == 4) {
     if (ctx->gemm) rc = launch_gemm32(ctx->N, ea, st);
-    else if (split_volume32(ctx->N)) rc = enqueue_split_stage(ctx, ea, st);
+    else if (split_volume32(ctx->N) && !ctx->d_Dn) rc = enqueue_split_stage(ctx, ea, st);
     else rc = launch_edge_vol32(ctx->N, ea, st);
   } else {
     rc = launch_edge_vol64(ctx->N, ea, st);
@@ -1104,6 +1155,21 @@ int rdg_reference_operator(int N, int which, double* out) {
     case 8:
       for (size_t i = 0; i < o->hyp.size(); ++i) out[i] = o->hyp[i];
       return RDG_OK;
+    case 9:
+      std::copy(o->RVV[0].begin(), o->RVV[0].end(), out);
+      std::copy(o->RVV[1].begin(), o->RVV[1].end(), out + o->RVV[0].size());
+      return RDG_OK;
+    case 10:
+    case 11: {
+      size_t off = 0;
+      for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) {
+          const std::vector<double>& g = which == 10 ? o->GR[j][k] : o->GS[j][k];
+          std::copy(g.begin(), g.end(), out + off);
+          off += g.size();
+        }
+      return RDG_OK;
+    }
     default: return RDG_EINVAL;
   }
   std::copy(src->begin(), src->end(), out);

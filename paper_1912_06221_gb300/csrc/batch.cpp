@@ -38,6 +38,7 @@ struct rdg_batch {
   // persistent form: one launch per chunk of steps of every member
   int mode = RDG_BATCH_AUTO;
   int ept[7] = {1, 1, 1, 1, 1, 1, 1};   // edges per thread of an edge tile, per order
+  int tpi[7] = {1, 1, 1, 1, 1, 1, 1};   // tiles per work item, per order
   double wait_s = 1.0;                  // bound on every dependency wait of the kernel
   int hold_member = -1;                 // test hook: this member's phase hold_phase never starts
   int64_t hold_phase = -1;
@@ -88,7 +89,7 @@ void release_member(rdg_batch::Member& m) {
 bool persistent_fits(const rdg_batch* b) {
   for (const auto& m : b->members) {
     const rdg_ctx* c = m.ctx;
-    if (c->esz != 4 || c->gemm || c->integrator != RDG_INTEGRATOR_SSP_RK3) return false;
+    if (c->esz != 4 || c->gemm || c->integrator != RDG_INTEGRATOR_SSP_RK3 || c->d_Dn) return false;
   }
   return !b->members.empty();
 }
@@ -148,11 +149,14 @@ int prepare_persistent(rdg_batch* b) {
     const int64_t per_tile = (int64_t)rdg::kStageBlock * d.ept;
     d.ntile_e = (c->E + per_tile - 1) / per_tile;
     d.ntile_u = d.ntile_v;
+    d.tpi = b->tpi[c->N];
+    d.nitem_a = (d.ntile_e + d.ntile_v + d.tpi - 1) / d.tpi;
+    d.nitem_b = (d.ntile_u + d.tpi - 1) / d.tpi;
     d.off_a = off;
     d.off_b = offb;
     d.hold_phase = i == b->hold_member ? b->hold_phase : -1;
-    off += d.ntile_e + d.ntile_v;
-    offb += d.ntile_u;
+    off += d.nitem_a;
+    offb += d.nitem_b;
     orders[c->N] = true;
   }
   std::vector<float> tabs;
@@ -183,10 +187,9 @@ int prepare_persistent(rdg_batch* b) {
   a.abort = b->d_flags;
   a.err = b->d_flags + 1;
   a.tabs = b->d_tabs;
-  for (int n = 0; n < 7; ++n) a.tab_off[n] = toff[n];
   a.tab_floats = (int)tabs.size();
   a.wait_ns = (uint64_t)(b->wait_s * 1e9);
-  b->smem = rdg::batch_smem_bytes(a.tab_floats);
+  b->smem = rdg::batch_smem_bytes(a.tab_floats, nm);
   b->grid = rdg::batch_grid(b->smem);
   if (b->grid <= 0) {
     free_persistent(b);
@@ -450,13 +453,15 @@ int rdg_batch_get_mode(const rdg_batch* b, int* mode) {
   return RDG_OK;
 }
 
-int rdg_batch_set_tiles(rdg_batch* b, int N, int edges_per_thread) {
+int rdg_batch_set_tiles(rdg_batch* b, int N, int edges_per_thread, int tiles_per_item) {
   if (!b) return RDG_EINVAL;
-  if (N < 1 || N > 6 || edges_per_thread < 1 || edges_per_thread > 2)
-    return bfail(b, RDG_EINVAL, "N must be in 1..6 and edges_per_thread 1 or 2");
+  if (N < 1 || N > 6 || edges_per_thread < 1 || edges_per_thread > 2 ||
+      (tiles_per_item != 1 && tiles_per_item != 2 && tiles_per_item != 4))
+    return bfail(b, RDG_EINVAL, "N must be in 1..6, edges_per_thread 1 or 2, tiles_per_item 1, 2 or 4");
   DevGuard g(b->device);
   cudaStreamSynchronize(b->stream);
   b->ept[N] = edges_per_thread;
+  b->tpi[N] = tiles_per_item;
   b->dirty = true;
   drop_graph(b);
   return RDG_OK;

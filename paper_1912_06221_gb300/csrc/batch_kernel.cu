@@ -13,8 +13,8 @@
 // its next item.
 //
 // The tiles do the work of the stage kernel and the element kernel (rhs_kernels.cuh) with
-// the same arithmetic; the per-order reference tables live in shared memory (every order of
-// the batch), so one kernel serves every order.  The paper solves one problem at a time; this
+// the same arithmetic; every order's reference matrices sit in constant memory (order 6's
+// volume matrices in shared memory), so one kernel serves every order.  The paper solves one problem at a time; this
 // has no counterpart there.
 #include <cuda_runtime.h>
 
@@ -37,6 +37,59 @@ namespace bk {
 
 using dev::Staged;
 using dev::stage_out;
+
+// Reference matrices of every order in constant memory (Dr, Ds, Wr, Ws, LIFT, the element
+// kernels' layout), so each entry is an immediate constant-bank operand as in the per-order
+// kernels; order 6's volume matrices are staged in shared memory instead (VolTab layout), as
+// the per-order stage kernel does.
+constexpr int tab_count(int N) { return 4 * np_of(N) * np_of(N) + 3 * np_of(N) * nfp_of(N); }
+__constant__ float c_b1[tab_count(1)];
+__constant__ float c_b2[tab_count(2)];
+__constant__ float c_b3[tab_count(3)];
+__constant__ float c_b4[tab_count(4)];
+__constant__ float c_b5[tab_count(5)];
+__constant__ float c_b6[tab_count(6)];
+
+template <int N>
+__device__ __forceinline__ float bt(int i) {
+  if constexpr (N == 1) return c_b1[i];
+  else if constexpr (N == 2) return c_b2[i];
+  else if constexpr (N == 3) return c_b3[i];
+  else if constexpr (N == 4) return c_b4[i];
+  else if constexpr (N == 5) return c_b5[i];
+  else return c_b6[i];
+}
+
+// The volume term of one element, the same arithmetic as volume_row (rhs_kernels.cuh) with the
+// constant table of order N.
+template <int N>
+__device__ __forceinline__ void volume_row_b(const float (&u)[np_of(N)], float ar, float as, float grr, float grs,
+                                             float gss, float (&vol)[np_of(N)]) {
+  constexpr int NP = np_of(N);
+  constexpr int ODR = 0, ODS = NP * NP, OWR = 2 * NP * NP, OWS = 3 * NP * NP;
+  float du[NP];
+#pragma unroll
+  for (int j = 1; j < NP; ++j) du[j] = u[j] - u[0];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) vol[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    float ur = 0.f, us = 0.f;
+#pragma unroll
+    for (int k = 1; k < NP; ++k) {
+      ur = fmaf(bt<N>(ODR + j * NP + k), du[k], ur);
+      us = fmaf(bt<N>(ODS + j * NP + k), du[k], us);
+    }
+    const float uj = j == 0 ? u[0] : du[j] + u[0];
+    const float fr = ar * uj - (grr * ur + grs * us);
+    const float fs = as * uj - (grs * ur + gss * us);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      vol[i] = fmaf(bt<N>(OWR + i * NP + j), fr, vol[i]);
+      vol[i] = fmaf(bt<N>(OWS + i * NP + j), fs, vol[i]);
+    }
+  }
+}
 
 __device__ __forceinline__ uint64_t gtime() {
   uint64_t t;
@@ -66,9 +119,10 @@ __device__ bool wait_count(const unsigned long long* cnt, unsigned long long tar
 // the stage (the element kernel's arithmetic, LIFT from the shared-memory table).  Its inputs
 // were written by other blocks of this launch: read through L2.
 template <int N, int MODE>
-__device__ __noinline__ void update_element(const BMember& b, int64_t k, const float* lift, const float* us,
-                                            const float* un, float* out, const float* tau) {
+__device__ __noinline__ void update_element(const BMember& b, int64_t k, const float* us, const float* un, float* out,
+                                            const float* tau) {
   constexpr int NP = np_of(N), NFP = nfp_of(N);
+  constexpr int OLIFT = 4 * NP * NP;
   const float ij = b.geo[5 * b.K + k];
   float rhs[NP];
 #pragma unroll
@@ -82,7 +136,7 @@ __device__ __noinline__ void update_element(const BMember& b, int64_t k, const f
     for (int i = 0; i < NP; ++i) {
       float acc = 0.f;
 #pragma unroll
-      for (int c = 0; c < NFP; ++c) acc = fmaf(lift[i * 3 * NFP + f * NFP + c], q[c], acc);
+      for (int c = 0; c < NFP; ++c) acc = fmaf(bt<N>(OLIFT + i * 3 * NFP + f * NFP + c), q[c], acc);
       rhs[i] -= ij * acc;
     }
   }
@@ -117,10 +171,9 @@ __device__ __noinline__ void run_tile(const BMember& b, bool part_b, int stage, 
     __syncthreads();
     const int64_t k = t * kStageBlock + threadIdx.x;
     if (k < b.K) {
-      const float* lift = tab + dev::VolTab<float, N>::SIZE;
-      if (stage == 0) update_element<N, 1>(b, k, lift, us, un, out, tau);
-      else if (stage == 1) update_element<N, 2>(b, k, lift, us, un, out, tau);
-      else update_element<N, 3>(b, k, lift, us, un, out, tau);
+      if (stage == 0) update_element<N, 1>(b, k, us, un, out, tau);
+      else if (stage == 1) update_element<N, 2>(b, k, us, un, out, tau);
+      else update_element<N, 3>(b, k, us, un, out, tau);
     }
     return;
   }
@@ -142,8 +195,11 @@ __device__ __noinline__ void run_tile(const BMember& b, bool part_b, int stage, 
       float u[NP], vol[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) u[j] = sh[tid * NP + j];
-      dev::volume_row_smem<float, N>(u, b.geo[k], b.geo[b.K + k], b.geo[2 * b.K + k], b.geo[3 * b.K + k],
-                                     b.geo[4 * b.K + k], tab, vol);
+      if constexpr (N >= 6)
+        dev::volume_row_smem<float, N>(u, b.geo[k], b.geo[b.K + k], b.geo[2 * b.K + k], b.geo[3 * b.K + k],
+                                       b.geo[4 * b.K + k], tab, vol);
+      else
+        volume_row_b<N>(u, b.geo[k], b.geo[b.K + k], b.geo[2 * b.K + k], b.geo[3 * b.K + k], b.geo[4 * b.K + k], vol);
 #pragma unroll
       for (int j = 0; j < NP; ++j) sh[tid * NP + j] = vol[j];
     }
@@ -162,16 +218,30 @@ __device__ __noinline__ void run_tile(const BMember& b, bool part_b, int stage, 
 
 __global__ void __launch_bounds__(kStageBlock, 4) batch_persistent_kernel(BatchArgs a) {
   extern __shared__ __align__(16) float smem[];
-  float* tabs = smem;                           // every order's tables, a.tab_floats
+  float* tabs = smem;                           // order 6's volume tables, if present
   float* sh = smem + a.tab_floats;              // element rows of a volume tile
+  // the member descriptors, in shared memory when they fit (searched for every item)
+  BMember* smem_m = reinterpret_cast<BMember*>(sh + kStageBlock * np_of(6));
+  const bool in_smem = a.nm <= kSmemMembers;
+  const BMember* mem = in_smem ? smem_m : a.m;
   __shared__ float tau[RDG_MAX_FORCING_TERMS];
   __shared__ long long s_item;
   __shared__ int s_go;
   for (int i = threadIdx.x; i < a.tab_floats; i += blockDim.x) tabs[i] = a.tabs[i];
-  __syncthreads();
+  if (in_smem) {
+    const int words = a.nm * (int)(sizeof(BMember) / 4);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(a.m);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(smem_m);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
   const long long total = a.per_phase * a.nphase;
+  // the next ticket is taken while the current item runs, hiding the atomic's round trip
+  long long next = threadIdx.x == 0 ? (long long)atomicAdd(a.ticket, 1ull) : 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.ticket, 1ull);
+    if (threadIdx.x == 0) {
+      s_item = next;
+      if (next < total) next = (long long)atomicAdd(a.ticket, 1ull);
+    }
     __syncthreads();
     const long long it = s_item;
     if (it >= total) break;
@@ -182,17 +252,16 @@ __global__ void __launch_bounds__(kStageBlock, 4) batch_persistent_kernel(BatchA
     int lo = 0, hi = a.nm - 1;                  // member holding item r of the part
     while (lo < hi) {
       const int mid = (lo + hi + 1) / 2;
-      if ((part_b ? a.m[mid].off_b : a.m[mid].off_a) <= r) lo = mid;
+      if ((part_b ? mem[mid].off_b : mem[mid].off_a) <= r) lo = mid;
       else hi = mid - 1;
     }
-    const BMember& b = a.m[lo];
-    const long long t = r - (part_b ? b.off_b : b.off_a);
+    const BMember& b = mem[lo];
     if (threadIdx.x == 0) {
       // part A of stage p after part B of stage p - 1; part B of stage p after part A of
       // stage p; a held stage's part A never starts
-      const unsigned long long na = (unsigned long long)(b.ntile_e + b.ntile_v), nb = (unsigned long long)b.ntile_u;
       const unsigned long long* cnt = part_b ? a.done + lo : a.done + a.nm + lo;
-      unsigned long long target = part_b ? (unsigned long long)(p + 1) * na : (unsigned long long)p * nb;
+      unsigned long long target = part_b ? (unsigned long long)(p + 1) * (unsigned long long)b.nitem_a
+                                         : (unsigned long long)p * (unsigned long long)b.nitem_b;
       if (!part_b && p == b.hold_phase) target = ~0ull;
       const bool ok = wait_count(cnt, target, a.abort, a.wait_ns);
       if (!ok) {
@@ -203,16 +272,21 @@ __global__ void __launch_bounds__(kStageBlock, 4) batch_persistent_kernel(BatchA
     }
     __syncthreads();
     if (!s_go) break;
+    const long long item = r - (part_b ? b.off_b : b.off_a);
+    const long long ntile = part_b ? b.ntile_u : b.ntile_e + b.ntile_v;
+    const long long t0 = item * b.tpi, t1 = min(t0 + b.tpi, ntile);
     const int step = p / 3, stage = p - 3 * step;
     const double tstep = b.ts->t0 + ((double)b.ts->n + step) * b.dt;
-    const float* tab = tabs + a.tab_off[b.N];
-    switch (b.N) {
-      case 1: run_tile<1>(b, part_b, stage, tstep, t, tab, sh, tau); break;
-      case 2: run_tile<2>(b, part_b, stage, tstep, t, tab, sh, tau); break;
-      case 3: run_tile<3>(b, part_b, stage, tstep, t, tab, sh, tau); break;
-      case 4: run_tile<4>(b, part_b, stage, tstep, t, tab, sh, tau); break;
-      case 5: run_tile<5>(b, part_b, stage, tstep, t, tab, sh, tau); break;
-      default: run_tile<6>(b, part_b, stage, tstep, t, tab, sh, tau); break;
+    for (long long t = t0; t < t1; ++t) {
+      switch (b.N) {
+        case 1: run_tile<1>(b, part_b, stage, tstep, t, tabs, sh, tau); break;
+        case 2: run_tile<2>(b, part_b, stage, tstep, t, tabs, sh, tau); break;
+        case 3: run_tile<3>(b, part_b, stage, tstep, t, tabs, sh, tau); break;
+        case 4: run_tile<4>(b, part_b, stage, tstep, t, tabs, sh, tau); break;
+        case 5: run_tile<5>(b, part_b, stage, tstep, t, tabs, sh, tau); break;
+        default: run_tile<6>(b, part_b, stage, tstep, t, tabs, sh, tau); break;
+      }
+      __syncthreads();                          // the tile's shared rows before the next tile
     }
     __threadfence();                            // this thread's writes of the item
     __syncthreads();                            // ... and every other thread's
@@ -227,11 +301,11 @@ __global__ void batch_advance_kernel(BMember* m, int nm, long long steps) {
 
 }  // namespace bk
 
-// Tables of order N in the layout the kernel reads: the volume tables (VolTab: Dr, Ds
-// row-major, Wr^T, Ws^T, rows padded) then LIFT [Np][3 Nfp].
-static void append_tables(int N, std::vector<float>& out) {
-  const RefOps* o = get_refops(N, nullptr);
-  const int NP = np_of(N), NFP = nfp_of(N);
+// Order 6's volume tables in the layout volume_row_smem reads (VolTab: Dr, Ds row-major,
+// Wr^T, Ws^T, rows padded); the other orders read constant memory.
+static void append_voltab6(std::vector<float>& out) {
+  const RefOps* o = get_refops(6, nullptr);
+  const int NP = np_of(6);
   const int NPP = (NP * 4 + 15) / 16 * 4;
   std::vector<float> vt(4 * NP * NPP, 0.f);
   for (int r = 0; r < NP; ++r)
@@ -242,23 +316,41 @@ static void append_tables(int N, std::vector<float>& out) {
       vt[3 * NP * NPP + r * NPP + c] = (float)o->Ws[c * NP + r];
     }
   out.insert(out.end(), vt.begin(), vt.end());
-  for (int i = 0; i < NP * 3 * NFP; ++i) out.push_back((float)o->LIFT[i]);
-  while (out.size() % 4) out.push_back(0.f);      // next order's tables 16-byte aligned
+}
+
+template <int N, typename A>
+static int upload_const(A& arr) {
+  std::vector<float> t = pack_elem_table<float>(N);
+  if (t.size() * sizeof(float) != sizeof(arr)) return RDG_EINVAL;
+  return cudaMemcpyToSymbol(arr, t.data(), sizeof(arr)) == cudaSuccess ? RDG_OK : RDG_ECUDA;
 }
 
 int batch_tables(const bool orders[7], std::vector<float>& tabs, int off[7]) {
+  static bool uploaded[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return RDG_EINVAL;
+  if (!uploaded[dev]) {
+    int rc = RDG_OK;
+    if (rc == RDG_OK) rc = upload_const<1>(bk::c_b1);
+    if (rc == RDG_OK) rc = upload_const<2>(bk::c_b2);
+    if (rc == RDG_OK) rc = upload_const<3>(bk::c_b3);
+    if (rc == RDG_OK) rc = upload_const<4>(bk::c_b4);
+    if (rc == RDG_OK) rc = upload_const<5>(bk::c_b5);
+    if (rc == RDG_OK) rc = upload_const<6>(bk::c_b6);
+    if (rc != RDG_OK) return rc;
+    uploaded[dev] = true;
+  }
   tabs.clear();
   for (int N = 0; N <= 6; ++N) off[N] = 0;
-  for (int N = 1; N <= 6; ++N) {
-    if (!orders[N]) continue;
-    if (!get_refops(N, nullptr)) return RDG_EINVAL;
-    off[N] = (int)tabs.size();
-    append_tables(N, tabs);
-  }
+  if (orders[6]) append_voltab6(tabs);
   return RDG_OK;
 }
 
-size_t batch_smem_bytes(int tab_floats) { return ((size_t)tab_floats + kStageBlock * np_of(6)) * sizeof(float); }
+size_t batch_smem_bytes(int tab_floats, int nm) {
+  const size_t base = ((size_t)tab_floats + kStageBlock * np_of(6)) * sizeof(float);
+  return base + (nm <= kSmemMembers ? (size_t)nm * sizeof(BMember) : 0);
+}
 
 int batch_grid(size_t smem) {
   static bool attr = false;

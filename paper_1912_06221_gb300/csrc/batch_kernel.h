@@ -32,8 +32,10 @@ struct BMember {
   float dt32;
   int N;
   int ept;                   // edges per thread in an edge tile (1 or 2)
+  int tpi;                   // tiles per work item (1, 2 or 4)
   int64_t ntile_e, ntile_v;  // part A: edge and element tiles per stage
   int64_t ntile_u;           // part B: element tiles per stage
+  int64_t nitem_a, nitem_b;  // work items of part A / part B per stage (tiles / tpi, rounded up)
   int64_t off_a, off_b;      // first item of this member within part A / part B of a stage
   int64_t hold_phase;        // a stage whose part A is never released (test hook), or -1
 };
@@ -48,15 +50,19 @@ struct BatchArgs {
   unsigned long long* done;  // [2 nm]: part-A items finished per member, then part-B items
   int* abort;
   int* err;                  // the batch's device error word
-  const float* tabs;         // per-order tables (batch_tables)
-  int tab_off[7];
+  const float* tabs;         // order 6's volume tables for shared memory (batch_tables), if present
   int tab_floats;
   uint64_t wait_ns;          // bound on every dependency wait
 };
 
-// Tables of the orders present (orders[N]) in one array, offsets per order.
+// Uploads every order's reference matrices to the kernel's constant banks (once per device)
+// and returns the shared-memory tables the kernel stages (order 6's volume matrices, when
+// orders[6]); off is unused (all zero).
 int batch_tables(const bool orders[7], std::vector<float>& tabs, int off[7]);
-size_t batch_smem_bytes(int tab_floats);
+// Dynamic shared memory of the kernel: the tables, a volume tile's rows, and the member
+// descriptors when there are at most kSmemMembers of them.
+constexpr int kSmemMembers = 64;
+size_t batch_smem_bytes(int tab_floats, int nm);
 int batch_grid(size_t smem);   // resident blocks of the persistent kernel (-1 on error)
 int launch_batch_persistent(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 int launch_batch_advance(BMember* m, int nm, long long steps, cudaStream_t s);

@@ -39,6 +39,8 @@ struct rdg_ctx {
   double vx = 0, vy = 0;
   std::vector<double> Dk;           // element diffusion (x diffusion when Dy is set)
   std::vector<double> Dy;           // y diffusion of a diagonal tensor (Dx, Dy); empty: isotropic
+  std::vector<double> Dn;           // D at the nodes [K][Np]; empty: D per element
+  void* d_Dn = nullptr;             // the same on the device, in the context's precision
   // device buffers
   int integrator = RDG_INTEGRATOR_SSP_RK3;
   bool gemm = false;                // GEMM form of the edge flux (RDG_FP32_3XTF32, N <= kMaxGemmN)

@@ -63,6 +63,7 @@ struct EdgeArgs {
   const int32_t* f12;  // fused form: per edge f1 | f2 << 2 (local faces of the two sides)
   T* fb;               // fused form: face fluxes [K][3][Nfp] in each element's own face order
   int64_t keep_tiles;  // operator tiles [0, keep_tiles) are loaded evict-last (kept in L2)
+  const T* Dn;         // D at the nodes [K][Np] when given so (geo then holds the metric alone), else null
 };
 
 // Device error bits reported through rdg_synchronize.
@@ -126,6 +127,8 @@ struct EdgeSetupIn {
   const double* shift;     // [E][2]
   const double* D;         // [K] (x diffusion when Dy is set)
   const double* Dy;        // [K] y diffusion of the diagonal tensor (Dx, Dy), or null: isotropic
+  const double* Dn;        // [K][Np] D at the nodes, or null (D then per element)
+  const double* nodal_refs;  // with Dn: RVV [2][Nfp][Np], GR [2][2][Np][Np], GS [2][2][Np][Np]
   const double* refs;      // per-order reference constants (layout in setup.cu)
   int64_t E;
   double vx, vy;

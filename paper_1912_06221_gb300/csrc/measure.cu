@@ -65,6 +65,26 @@ int peak_fma(int device, double* flops) {
   return rc;
 }
 
+// Streaming read of n4 16-byte words: grid-stride, eight independent evict-first loads per
+// trip, summed in a register that is stored only under a condition that never holds.
+__global__ void __launch_bounds__(256) stream_read_kernel(const float4* __restrict__ p, int64_t n4, float* out) {
+  float acc = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 7 * stride < n4; i += 8 * stride) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u].x + v[u].y + v[u].z + v[u].w;
+  }
+  for (; i < n4; i += stride) {
+    const float4 v = __ldcs(p + i);
+    acc += v.x + v.y + v.z + v.w;
+  }
+  if (acc == -1.f) out[blockIdx.x] = acc;
+}
+
 // Collapsed Gauss rule on the reference triangle with q = N + 3 points per direction: exact
 // for total degree 2q - 2 = 2N + 4 (the degree of the squared error of a degree-(N + 2)
 // function), weights summing to the reference area 2.
@@ -151,6 +171,55 @@ extern "C" int rdg_peak_fma(int device, int precision, double* flops_per_second)
   const int rc = precision == RDG_FP32 ? peak_fma<float>(device, flops_per_second) : peak_fma<double>(device, flops_per_second);
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
   return rc;
+}
+
+extern "C" int rdg_stream_read(int device, int64_t bytes, double* seconds) {
+  using namespace rdg;
+  if (!seconds || bytes < 16 || bytes > ((int64_t)64 << 30)) return RDG_EINVAL;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return RDG_EINVAL;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device && cudaSetDevice(device) != cudaSuccess) return RDG_ECUDA;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  const int64_t n4 = bytes / 16;
+  const size_t flush_bytes = (size_t)512 << 20;    // larger than L2: written between timed reads
+  float4* buf = nullptr;
+  float* out = nullptr;
+  void* flush = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = RDG_OK;
+  if (cudaMalloc(&buf, (size_t)n4 * 16) != cudaSuccess || cudaMalloc(&out, 8192 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&flush, flush_bytes) != cudaSuccess)
+    rc = RDG_ENOMEM;
+  if (rc == RDG_OK && (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = RDG_ECUDA;
+  std::vector<float> ts;
+  if (rc == RDG_OK) cudaMemsetAsync(buf, 0, (size_t)n4 * 16, s);
+  for (int rep = 0; rc == RDG_OK && rep < 10; ++rep) {   // two warm-up reads, median of eight
+    cudaMemsetAsync(flush, rep, flush_bytes, s);
+    cudaEventRecord(e0, s);
+    stream_read_kernel<<<nsm * 8, 256, 0, s>>>(buf, n4, out);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = RDG_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep >= 2) ts.push_back(ms);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(buf);
+  cudaFree(out);
+  cudaFree(flush);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  if (rc != RDG_OK) return rc;
+  std::sort(ts.begin(), ts.end());
+  *seconds = 0.5 * (ts[ts.size() / 2 - 1] + ts[ts.size() / 2]) * 1e-3;
+  return RDG_OK;
 }
 
 extern "C" int rdg_error_quadrature(rdg_ctx* ctx, int* nq, double* xy) {

@@ -364,6 +364,13 @@ std::unique_ptr<RefOps> build(int N, const char** err) {
     for (int j = 0; j < 2; ++j) {
       const double sj = j == 0 ? 1.0 : -1.0;
       Mat PA = matmul(Phi, Ap[j], Nfp, Mp, Np);
+      o->RVV[j] = matmul(PA, o->Vinv, Nfp, Np, Np);
+      Mat DrVA = matmul(matmul(o->Dr, o->V, Np, Np, Np), Ak[j], Np, Np, Mp);
+      Mat DsVA = matmul(matmul(o->Ds, o->V, Np, Np, Np), Ak[j], Np, Np, Mp);
+      for (int k = 0; k < 2; ++k) {
+        o->GR[j][k] = matmul(matmul(DrVA, Ap[k], Np, Mp, Np), o->Vinv, Np, Np, Np);
+        o->GS[j][k] = matmul(matmul(DsVA, Ap[k], Np, Mp, Np), o->Vinv, Np, Np, Np);
+      }
       Mat YR = matmul(matmul(PA, DrM, Nfp, Np, Np), Ak[j], Nfp, Np, Mp);
       Mat YS = matmul(matmul(PA, DsM, Nfp, Np, Np), Ak[j], Nfp, Np, Mp);
       for (auto& y : YR) y *= sj;

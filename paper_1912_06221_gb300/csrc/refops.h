@@ -47,6 +47,11 @@ struct RefOps {
   // summed over input sides k, with ZR[j][k] = Y^R_j A+_k Vinv, Y^R_j = s_j Phi_diag A+_j
   // (Vinv Dr V) A_j (s_1 = 1, s_2 = -1 for side 2's reflected frame), [Nfp][Np] each.
   std::vector<double> ZR[2][2], ZS[2][2];
+  // The same factors split where a nodal D enters (D given at the nodes, multiplied into the
+  // sub-triangle's nodal gradient): ZR[j][k] = s_j RVV[j] diag(1) GR[j][k] with
+  // RVV[j] = Phi_diag A+_j Vinv [Nfp][Np] (also the reconstruction of nodal data of side j on
+  // the diagonal, Algorithm 2) and GR[j][k] = Dr V A_j A+_k Vinv, GS likewise, [Np][Np].
+  std::vector<double> RVV[2], GR[2][2], GS[2][2];
   std::vector<int> hyp;              // [Nfp] rotated-order indices of the shared face's nodes
 };
 

@@ -91,9 +91,12 @@ __device__ __forceinline__ void report(int* err, int bit) {
 // multiplies differences of nearby values rather than u itself.  Evaluated node by node as a
 // running outer product (F_r, F_s at node j, then their column j of Wr, Ws into vol), so only
 // u - u_0 and vol are live: 2 Np values instead of 5 Np.
-template <typename T, int N>
+//
+// NODAL: D given at the nodes (dn, the element's Np values; the coefficients g_rr, g_rs, g_ss
+// then hold the metric alone), F_r = a_r u - D_j (g_rr u_r + g_rs u_s) node by node.
+template <typename T, int N, bool NODAL = false>
 __device__ __forceinline__ void volume_row(const T (&u)[np_of(N)], T ar, T as, T grr, T grs, T gss,
-                                           T (&vol)[np_of(N)]) {
+                                           T (&vol)[np_of(N)], const T* __restrict__ dn = nullptr) {
   constexpr int NP = np_of(N);
   constexpr int ODR = 0, ODS = NP * NP, OWR = 2 * NP * NP, OWS = 3 * NP * NP;
   T du[NP];
@@ -110,8 +113,15 @@ __device__ __forceinline__ void volume_row(const T (&u)[np_of(N)], T ar, T as, T
       us = fma((T)RDG_TAB[ODS + j * NP + k], du[k], us);
     }
     const T uj = j == 0 ? u[0] : du[j] + u[0];
-    const T fr = ar * uj - (grr * ur + grs * us);
-    const T fs = as * uj - (grs * ur + gss * us);
+    T fr, fs;
+    if constexpr (NODAL) {
+      const T dj = __ldg(dn + j);
+      fr = ar * uj - dj * (grr * ur + grs * us);
+      fs = as * uj - dj * (grs * ur + gss * us);
+    } else {
+      fr = ar * uj - (grr * ur + grs * us);
+      fs = as * uj - (grs * ur + gss * us);
+    }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       vol[i] = fma((T)RDG_TAB[OWR + i * NP + j], fr, vol[i]);
@@ -132,9 +142,10 @@ struct VolTab {
   static constexpr int SIZE = 4 * NP * NPP;
 };
 
-template <typename T, int N>
+template <typename T, int N, bool NODAL = false>
 __device__ __forceinline__ void volume_row_smem(const T (&u)[np_of(N)], T ar, T as, T grr, T grs, T gss,
-                                                const T* __restrict__ tab, T (&vol)[np_of(N)]) {
+                                                const T* __restrict__ tab, T (&vol)[np_of(N)],
+                                                const T* __restrict__ dn = nullptr) {
   using VT = VolTab<T, N>;
   constexpr int NP = VT::NP, NPP = VT::NPP;
   T du[NP];
@@ -158,8 +169,15 @@ __device__ __forceinline__ void volume_row_smem(const T (&u)[np_of(N)], T ar, T 
     T uj = u[0];
 #pragma unroll
     for (int k = 1; k < NP; ++k) uj = (k == j) ? du[k] + u[0] : uj;
-    const T fr = ar * uj - (grr * ur + grs * us);
-    const T fs = as * uj - (grs * ur + gss * us);
+    T fr, fs;
+    if constexpr (NODAL) {
+      const T dj = __ldg(dn + j);
+      fr = ar * uj - dj * (grr * ur + grs * us);
+      fs = as * uj - dj * (grs * ur + gss * us);
+    } else {
+      fr = ar * uj - (grr * ur + grs * us);
+      fs = as * uj - (grs * ur + gss * us);
+    }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       vol[i] = fma(WrT[i], fr, vol[i]);
@@ -235,7 +253,7 @@ __device__ __forceinline__ void stage_out(T* g, const T* sh, int n) {
 // Volume role of the stage kernel: element tile v (one thread per element, rows staged
 // through shared memory), vol = M^{-1} S^T . F written to a.vol.  Kept out of line so its
 // register demand does not set the edge role's.
-template <typename T, int N>
+template <typename T, int N, bool NODAL = false>
 __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, T* sh) {
   constexpr int NP = np_of(N);
   constexpr bool SMEM_TAB = N >= 6 && sizeof(T) == 4;   // (FP64: 25 KB of tables, and FP64-bound anyway)
@@ -260,11 +278,13 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
     T u[NP], vol[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) u[j] = sh[tid * NP + j];
+    const T* dn = NODAL ? a.Dn + k * NP : nullptr;
     if constexpr (SMEM_TAB)
-      volume_row_smem<T, N>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k],
-                            tab, vol);
+      volume_row_smem<T, N, NODAL>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k],
+                                   a.geo[4 * a.K + k], tab, vol, dn);
     else
-      volume_row<T, N>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k], vol);
+      volume_row<T, N, NODAL>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k],
+                              vol, dn);
 #pragma unroll
     for (int j = 0; j < NP; ++j) sh[tid * NP + j] = vol[j];   // a thread rewrites only its own row
   }
@@ -397,7 +417,8 @@ __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N, KIND>()) e
     const int64_t b = blockIdx.x;
     const int64_t v0 = (b * nv) / nb, v1 = ((b + 1) * nv) / nb;
     if (v1 > v0) {
-      stage_volume_tile<T, N>(a, v0, sh);
+      if (a.Dn) stage_volume_tile<T, N, true>(a, v0, sh);    // D given at the nodes
+      else stage_volume_tile<T, N, false>(a, v0, sh);
       return;
     }
     eblk = b - v1;    // edge blocks so far = blocks so far minus volume blocks so far

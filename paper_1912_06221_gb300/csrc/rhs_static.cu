@@ -44,6 +44,8 @@ extern "C" int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_de
     return fail_static(ctx, RDG_ESTATE,
                        "rdg_rhs_eval_static needs stored flux operators: contexts using the GEMM form of the edge "
                        "flux (RDG_FP32_3XTF32 with N <= 5 and an interface rule other than RDG_IFACE_ALG1) are refused");
+  if (ctx->d_Dn)
+    return fail_static(ctx, RDG_ESTATE, "rdg_rhs_eval_static does not take a D given at the nodes");
   const size_t need = (size_t)ctx->E * nfp_of(ctx->N) * ctx->esz;
   if (need > kStaticFluxBytes)
     return fail_static(ctx, RDG_EINVAL,

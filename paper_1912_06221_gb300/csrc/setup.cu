@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   __shared__ double sVp[WARPS][NP * NP];
   __shared__ double sK[WARPS][NFP * NP];
   __shared__ double sB[WARPS][NFP * NP];
+  __shared__ double sD[WARPS][2 * NP + NFP];   // nodal D: d_j at side j's sub-triangle nodes, then D~_i
   for (int i = threadIdx.x; i < RT; i += blockDim.x) sR[i] = in.refs[i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -235,6 +236,83 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   const double vn = n1.x * in.vx + n1.y * in.vy;
   const int ff[2] = {f1, f2};
   const int64_t tile = e >> 5, le = e & 31;
+  const bool nodal = in.Dn != nullptr;
+  if (nodal) {
+    // D at each side's sub-triangle nodes: d_j = V_pj V_rf^{-1} D_j, the element's nodal D
+    // (a ghost: its element's D at the reflected points) in the rotated order of the side's face
+    double* dn = sB[warp];                  // scratch: the side's nodal D, then its modal values
+    for (int side = 0; side < 2; ++side) {
+      const int kk = side == 0 ? k1 : k2;
+      if (kk >= 0) {
+        if (lane < NP) dn[lane] = in.Dn[(int64_t)kk * NP + lane];
+      } else {
+        // a ghost's node (barycentric l1, l2, l3 on its vertices: reflected apex, e2, e1) is
+        // the reflection of element k1's point with l1 at its apex, l2 at e1 and l3 at e2, so
+        // the ghost's D there is k1's D at that point: k1's modal D, evaluated
+        double modal = 0.0;
+        if (lane < NP)
+          for (int l = 0; l < NP; ++l) modal = fma(Vinv[lane * NP + l], in.Dn[(int64_t)k1 * NP + l], modal);
+        if (lane < NP) dn[NP + lane] = modal;
+        __syncwarp();
+        double val = 0.0;
+        if (lane < NP) {
+          const double l1 = -(rr[lane] + ss[lane]) / 2, l2 = (rr[lane] + 1) / 2, l3 = (ss[lane] + 1) / 2;
+          double L[3];
+          L[fc[f1]] = l1;
+          L[fa[f1]] = l2;
+          L[fb[f1]] = l3;
+          double ph[NP];
+          simplex_basis_tab<N>(2 * L[1] - 1, 2 * L[2] - 1, jac, ph);
+          for (int m = 0; m < NP; ++m) val = fma(ph[m], dn[NP + m], val);
+        }
+        __syncwarp();
+        if (lane < NP) dn[lane] = val;
+      }
+      __syncwarp();
+      // modal coefficients of the rotated nodal D, then values at the sub-triangle nodes
+      const int f = ff[side];
+      double mo = 0.0;
+      if (lane < NP)
+        for (int l = 0; l < NP; ++l) mo = fma(Vinv[lane * NP + l], dn[(int)perminv[f * NP + l]], mo);
+      __syncwarp();
+      if (lane < NP) dn[NP + lane] = mo;
+      if (lane < NP) {
+        const double rn = rr[lane], sn = ss[lane];
+        const double Ar = -(rn + sn) / 2 * al[side] + (rn + 1) / 2 - (sn + 1) / 2;
+        const double As = -(rn + sn) / 2 * be[side] - (rn + 1) / 2 + (sn + 1) / 2;
+        simplex_basis_tab<N>(Ar, As, jac, &sVp[warp][lane * NP]);
+      }
+      __syncwarp();
+      if (lane < NP) {
+        double d = 0.0;
+        for (int m = 0; m < NP; ++m) d = fma(sVp[warp][lane * NP + m], dn[NP + m], d);
+        sD[warp][side * NP + lane] = d;
+      }
+      __syncwarp();
+    }
+    // edge coefficient per diagonal node: Algorithm 2 reconstructs D from both sides' nodal
+    // data (D~ = sum_j RVV_j d_j); the harmonic rule takes the two traces at the face node
+    if (lane < NFP) {
+      const int i = lane;
+      double dt;
+      if (in.iface == RDG_IFACE_HARMONIC) {
+        const double t1 = in.Dn[(int64_t)k1 * NP + (int)fmask[f1 * NFP + i]];
+        // side 2's face node matching side 1's node i (its face runs the other way)
+        const int col2 = (int)fmask[f2 * NFP + (NFP - 1 - i)];
+        // (a ghost's D at that point is its element's at the mirrored face node)
+        const double t2 = k2 >= 0 ? in.Dn[(int64_t)k2 * NP + col2]
+                                  : in.Dn[(int64_t)k1 * NP + (int)fmask[f1 * NFP + (NFP - 1 - i)]];
+        dt = 2.0 * t1 * t2 / (t1 + t2);
+      } else {
+        const double* RVV = in.nodal_refs;
+        dt = 0.0;
+        for (int j = 0; j < 2; ++j)
+          for (int n = 0; n < NP; ++n) dt = fma(RVV[(j * NFP + i) * NP + n], sD[warp][j * NP + n], dt);
+      }
+      sD[warp][2 * NP + i] = dt;
+    }
+    __syncwarp();
+  }
   const int VW = 16 / elem_bytes;
   const int QW = (NFP * (2 * NP - 1) + 1 + VW - 1) / VW;   // 16-byte words of the stored operator
 
@@ -271,7 +349,26 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
     }
     const double* QRV = QV + (2 * side) * NFP * NP;
     const double* QSV = QV + (2 * side + 1) * NFP * NP;
-    if (in.iface == RDG_IFACE_ALG1 && aniso) {
+    if (in.iface == RDG_IFACE_ALG1 && nodal) {
+      // Algorithm 1 with D at the sub-triangle nodes: sum_j s_j RVV_j diag(d_j)
+      // (kappa_R GR[j][side] + kappa_S GS[j][side])
+      const double* RVV = in.nodal_refs;
+      const double* GRb = RVV + 2 * NFP * NP;
+      const double* GSb = GRb + 4 * NP * NP;
+      for (int t = lane; t < NFP * NP; t += 32) {
+        const int i = t / NP, l = t % NP;
+        double acc = 0.0;
+        for (int j = 0; j < 2; ++j) {
+          const double sj = j == 0 ? 1.0 : -1.0;
+          const double* gr = GRb + (j * 2 + side) * NP * NP;
+          const double* gs = GSb + (j * 2 + side) * NP * NP;
+          for (int n = 0; n < NP; ++n)
+            acc = fma(sj * RVV[(j * NFP + i) * NP + n] * sD[warp][j * NP + n], kR * gr[n * NP + l] + kS * gs[n * NP + l],
+                      acc);
+        }
+        sK[warp][t] = acc;
+      }
+    } else if (in.iface == RDG_IFACE_ALG1 && aniso) {
       // Algorithm 1 with D = (Dx, Dy): sub-triangle j's product is (Dx^j u~_x, Dy^j u~_y), so its
       // R and S parts carry n_x Dx^j R_x + n_y Dy^j R_y and n_x Dx^j S_x + n_y Dy^j S_y
       const double* Z = zq + side * 4 * NFP * NP;
@@ -314,6 +411,7 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
       for (int j = 0; j < NP; ++j) c = fma(sB[warp][i * NP + j], Vinv[j * NP + l], c);
       const int col = (int)perminv[f * NP + l];
       const double Dt = (in.iface == RDG_IFACE_ALG1 || aniso) ? 1.0   // D inside the factors
+                        : nodal                                   ? sD[warp][2 * NP + i]
                         : in.iface == RDG_IFACE_HARMONIC ? 2.0 * D1v * D2v / (D1v + D2v)
                                                          : D1v * dvec[i] + D2v * dvec[NFP + i];
       double w = -Jf * Dt * c;
@@ -355,7 +453,7 @@ __global__ void elem_setup_kernel(int64_t K, const double* xy, const double* D, 
   const double J = xr * ys - xs * yr;
   const double rx = ys / J, ry = -xs / J, sx = -yr / J, sy = xr / J;
   // F_r = r . F, F_s = s . F with F = v u - (Dx u_x, Dy u_y): g_ab = Dx a_x b_x + Dy a_y b_y
-  const double Dx = D[k];
+  const double Dx = D ? D[k] : 1.0;   // null: D given at the nodes, the metric alone here
   double g[6] = {rx * vx + ry * vy, sx * vx + sy * vy, Dx * (rx * rx + ry * ry), Dx * (rx * sx + ry * sy),
                  Dx * (sx * sx + sy * sy), 1.0 / J};
   if (Dy) {

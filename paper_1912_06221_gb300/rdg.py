@@ -43,6 +43,7 @@ SIGNATURES = {
     "rdg_rows_scatter": (_INT, [_P, _P, _P, _I64, _P]),
     "rdg_operator_setup": (_INT, [_P, _INT, _P, _D, _D, _INT, _INT]),
     "rdg_operator_setup_aniso": (_INT, [_P, _INT, _P, _P, _D, _D, _INT, _INT]),
+    "rdg_operator_setup_nodal": (_INT, [_P, _INT, _P, _D, _D, _INT, _INT]),
     "rdg_set_forcing": (_INT, [_P, _INT, _P, _P, _P, _INT, _P, _P, _P]),
     "rdg_mesh_counts": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "rdg_get_node_coords": (_INT, [_P, _P]),
@@ -64,6 +65,7 @@ SIGNATURES = {
     "rdg_error_quadrature": (_INT, [_P, ctypes.POINTER(_INT), _P]),
     "rdg_error_norms": (_INT, [_P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rdg_peak_fma": (_INT, [_INT, _INT, ctypes.POINTER(_D)]),
+    "rdg_stream_read": (_INT, [_INT, _I64, ctypes.POINTER(_D)]),
     "rdg_batch_create": (_INT, [ctypes.POINTER(_P), _INT, _P, _INT]),
     "rdg_batch_destroy": (_INT, [_P]),
     "rdg_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -75,7 +77,7 @@ SIGNATURES = {
     "rdg_batch_synchronize": (_INT, [_P]),
     "rdg_batch_set_mode": (_INT, [_P, _INT]),
     "rdg_batch_get_mode": (_INT, [_P, ctypes.POINTER(_INT)]),
-    "rdg_batch_set_tiles": (_INT, [_P, _INT, _INT]),
+    "rdg_batch_set_tiles": (_INT, [_P, _INT, _INT, _INT]),
     "rdg_batch_set_wait_limit": (_INT, [_P, _D]),
     "rdg_batch_hold_phase": (_INT, [_P, _INT, _I64]),
 }
@@ -132,10 +134,18 @@ def peak_fma(device=0, precision=FP32):
     return out.value
 
 
+def stream_read_seconds(device=0, nbytes=1 << 30):
+    """Time of a plain streaming read of nbytes from device memory (rdg_stream_read)."""
+    out = _D(0.0)
+    _check(load().rdg_stream_read(device, int(nbytes), ctypes.byref(out)))
+    return out.value
+
+
 def reference_operator(N, which):
     Np, Nfp, Mp = np_of(N), N + 1, (N + 1) ** 2
     shape = {0: (2, Np), 1: (Np, Np), 2: (Np, Np), 3: (Np, 3 * Nfp), 4: (Mp, 2 * Np), 5: (Np, Np),
-             6: (2, Np, Nfp, 2, Np), 7: (3, Np), 8: (Nfp,)}[which]
+             6: (2, Np, Nfp, 2, Np), 7: (3, Np), 8: (Nfp,), 9: (2, Nfp, Np), 10: (2, 2, Np, Np),
+             11: (2, 2, Np, Np)}[which]
     out = np.zeros(shape)
     _check(load().rdg_reference_operator(N, which, _ptr(out)))
     return out
@@ -170,7 +180,10 @@ class Solver:
                        _ptr(per) if period is not None else None, int(n_owned))
         self.n_owned = tri.shape[0] if n_owned is None else int(n_owned)
         Da = np.asarray(D_elem, np.float64)
-        if Da.ndim == 2:        # [nt, 2]: the diagonal tensor (Dx, Dy)
+        if Da.ndim == 2 and Da.shape[1] == self.Np:     # [nt, Np]: D given at the nodes
+            Dn = np.ascontiguousarray(Da)
+            self._call("rdg_operator_setup_nodal", N, _ptr(Dn), float(v[0]), float(v[1]), precision, interface)
+        elif Da.ndim == 2:        # [nt, 2]: the diagonal tensor (Dx, Dy)
             Dx = np.ascontiguousarray(Da[:, 0])
             Dy = np.ascontiguousarray(Da[:, 1])
             self._call("rdg_operator_setup_aniso", N, _ptr(Dx), _ptr(Dy), float(v[0]), float(v[1]), precision,
@@ -401,8 +414,8 @@ class Batch:
         self._call("rdg_batch_get_mode", ctypes.byref(m))
         return m.value
 
-    def set_tiles(self, N: int, edges_per_thread: int):
-        self._call("rdg_batch_set_tiles", int(N), int(edges_per_thread))
+    def set_tiles(self, N: int, edges_per_thread: int, tiles_per_item: int = 1):
+        self._call("rdg_batch_set_tiles", int(N), int(edges_per_thread), int(tiles_per_item))
 
     def set_wait_limit(self, seconds: float):
         self._call("rdg_batch_set_wait_limit", float(seconds))

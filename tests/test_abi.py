@@ -96,3 +96,26 @@ def test_solver_without_gpu_raises(lib):
     xy, tri = unit_square_mesh(4, 0.1, 1)
     with pytest.raises(Exception):
         rdg.Solver(xy, tri, 2, 1.0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 6])
+def test_library_nodal_D_factors_match_oracle(lib, N):
+    """The factors of a nodal D (RVV = Phi_diag A+_j Vinv, GR/GS = D V A_j A+_k Vinv), which do
+    not depend on the choice of orthonormal bases, equal the oracle's compositions, and
+    s_j RVV_j GR_jk summed with unit D gives back Algorithm 1's factor for constant D."""
+    import paper_1912_06221_gb300 as rdg
+    from oracle.refops import RefOps
+    o = RefOps(N)
+    Np = o.Np
+    Phi = o.phi(o.diag_R, o.diag_S)
+    A = [o.A1, o.A2]
+    Ap = [o.Apinv[:, :Np], o.Apinv[:, Np:]]
+    RVV = rdg.reference_operator(N, 9)
+    GR = rdg.reference_operator(N, 10)
+    GS = rdg.reference_operator(N, 11)
+    sc = (N + 1) ** 4
+    for j in range(2):
+        assert np.abs(RVV[j] - Phi @ Ap[j] @ o.Vinv).max() < 1e-11 * sc
+        for k in range(2):
+            assert np.abs(GR[j, k] - o.Dr @ o.V @ A[j] @ Ap[k] @ o.Vinv).max() < 1e-10 * sc
+            assert np.abs(GS[j, k] - o.Ds @ o.V @ A[j] @ Ap[k] @ o.Vinv).max() < 1e-10 * sc

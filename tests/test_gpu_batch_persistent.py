@@ -8,7 +8,8 @@ member is FP32 with stored operators and SSP-RK3): one launch per chunk of steps
   on the CUDA cores instead of the tensor cores, and forced members' stage times summed in
   another order) and the branch-graph form of the same batch; a small member follows the
   FP64 oracle.
-* Per-order tile mapping (two edges per thread) gives the same states.
+* Per-order tile mappings (one or two edges per thread, one to four tiles per work item) give
+  the same states.
 * Bounded waits: with a stage of one member held (a release that never comes) and a 50 ms
   limit, the launch gives up, returns, and the step reports RDG_ETIMEOUT; after the hold is
   removed the batch steps correctly again."""
@@ -68,8 +69,8 @@ def _batch(mode=rdg.BATCH_AUTO, ept=None):
     b = rdg.Batch(chunk=16)
     b.set_mode(mode)
     if ept:
-        for N, e in ept.items():
-            b.set_tiles(N, e)
+        for N, (e, tpi) in ept.items():
+            b.set_tiles(N, e, tpi)
     for s, u0, dt in members:
         b.add(s, dt, t0=0.25)
     return b, members
@@ -102,8 +103,8 @@ def test_persistent_batch_equals_alone_and_graph_form():
         s.close()
 
 
-def test_persistent_batch_two_edges_per_thread():
-    b, mem = _batch(ept={2: 2, 4: 2, 6: 2})
+def test_persistent_batch_tile_mappings():
+    b, mem = _batch(ept={1: (1, 4), 2: (2, 1), 3: (1, 2), 4: (2, 4), 5: (2, 2), 6: (2, 4)})
     b.step(40)
     b.synchronize()
     for i, (s, _, _) in enumerate(mem):

@@ -56,3 +56,14 @@ def test_fma_rates():
     # GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x ~2 GHz ~ 78 TFLOP/s; FP64 far below
     assert 2e13 < f32 < 2e14, f32
     assert 0 < f64 < f32, (f32, f64)
+
+
+def test_stream_read_bandwidth():
+    """A 1 GiB streaming read reaches a sizeable share of the HBM rate; a 64 MiB read, a
+    standalone launch with its fixed ramp-up, a smaller one."""
+    t_big = rdg.stream_read_seconds(0, 1 << 30)
+    t_small = rdg.stream_read_seconds(0, 64 << 20)
+    bw_big = (1 << 30) / t_big
+    bw_small = (64 << 20) / t_small
+    assert 2e12 < bw_big < 9e12, bw_big
+    assert bw_small < bw_big

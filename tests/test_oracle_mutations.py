@@ -187,3 +187,24 @@ def test_mutation_tensor_volume_uses_one_component(monkeypatch):
             self.D[:, 1] = self.D[:, 0]
     monkeypatch.setattr(orhs.Problem, "__init__", bad)
     _fails(TN.test_tensor_sin_mode_decay_rate, "alg1")
+
+
+def test_mutation_nodal_D_projection_skipped(monkeypatch):
+    """Algorithm 1 with nodal D using the element's nodal values as if they were the values at
+    the sub-triangle nodes (no V_p projection)."""
+    from tests import test_oracle_nodal as TD
+    orig = ardg.EdgeOps.flux_algorithm1
+
+    def bad(self, c, D1, D2):
+        D1, D2 = np.asarray(D1), np.asarray(D2)
+        if D1.ndim == 2 and D1.shape[1] == self.mesh.ops.Np:
+            P1, P2 = self.P1, self.P2
+            eye = np.broadcast_to(self.mesh.ops.Vinv, P1.shape)
+            self.P1, self.P2 = eye, eye
+            try:
+                return orig(self, c, D1, D2)
+            finally:
+                self.P1, self.P2 = P1, P2
+        return orig(self, c, D1, D2)
+    monkeypatch.setattr(ardg.EdgeOps, "flux_algorithm1", bad)
+    _fails(TD.test_nodal_D_exact_for_linear_D_and_polynomials, 3, "alg1")
