@@ -529,7 +529,23 @@ def run_ours(args):
         st_.synchronize()
         st_.close()
         u64 = u64s["harmonic"]
+        # its own roofline: per element per stage the state (3 Np values), 1.5 parameter
+        # records (16-byte words) and the coefficients and ids; the split products on the
+        # tensor cores (2 sides x NPAD x KP x 2 flop x 3 products per edge); TF32 peak = the
+        # measured bf16 burst rate x the nominal TF32/BF16 ratio 1.1/2.25
+        pw4 = (2 * Np + Nfp + 3 + 3) // 4
+        npad, kp = (Np * Nfp + 15) // 16 * 16, (2 * Np + 7) // 8 * 8
+        g_bytes = K * (4 * 3 * Np + 56) + E * pw4 * 16
+        g_flops = E * 2 * npad * kp * 2 * 3
+        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] * 1e12 \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1.9e15
+        p_tf32 = bf16 * 1.1 / 2.25
+        t_g = float(np.median(tt)) / 1e3 / (3 * nrk)
+        t_roof_g = max(g_bytes / (peak * 1e9), g_flops / p_tf32)
         tf32 = {"value": s.K * s.Np * 3 * nrk / (float(np.median(tt)) / 1e3) / 1e9, "unit": UNIT,
+                "roofline": {"alg_bytes_per_stage": g_bytes, "tensor_flops_per_stage": g_flops,
+                             "t_bytes_us": g_bytes / (peak * 1e9) * 1e6, "t_tensor_us": g_flops / p_tf32 * 1e6,
+                             "tf32_peak_tflops": p_tf32 / 1e12, "stage_us": t_g * 1e6, "frac": t_roof_g / t_g},
                 "kernel": "edge_gemm_kernel<4> (tcgen05.mma kind::tf32, split 3xTF32) + elem_lite_kernel",
                 "rel_l2_vs_fp64": float(np.linalg.norm(ut - u64) / np.linalg.norm(u64)),
                 "rel_linf_vs_fp64": float(np.abs(ut - u64).max() / np.abs(u64).max()),
