@@ -402,7 +402,7 @@ def run_ours(args):
     elem_avg = elem_ms / elem_n
     ach = stage_alg / (edge_avg / 1e3) / 1e9
     traffic, traffic_src = (None, "GEMM form: no capture") if gemm else profiled_traffic(args)
-    kname = "edge_gemm_kernel<4>" if gemm else "edge_flux_kernel<float,4,VOL=1>"
+    kname = "edge_gemm_pipe_kernel<4>" if gemm else "edge_flux_kernel<float,4,VOL=1>"
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind, "traffic": traffic,
@@ -546,7 +546,7 @@ def run_ours(args):
                 "roofline": {"alg_bytes_per_stage": g_bytes, "tensor_flops_per_stage": g_flops,
                              "t_bytes_us": g_bytes / (peak * 1e9) * 1e6, "t_tensor_us": g_flops / p_tf32 * 1e6,
                              "tf32_peak_tflops": p_tf32 / 1e12, "stage_us": t_g * 1e6, "frac": t_roof_g / t_g},
-                "kernel": "edge_gemm_kernel<4> (tcgen05.mma kind::tf32, split 3xTF32) + elem_lite_kernel",
+                "kernel": "edge_gemm_pipe_kernel<4> (warp-specialised, tcgen05.mma kind::tf32, split 3xTF32) + elem_lite_kernel",
                 "rel_l2_vs_fp64": float(np.linalg.norm(ut - u64) / np.linalg.norm(u64)),
                 "rel_linf_vs_fp64": float(np.abs(ut - u64).max() / np.abs(u64).max()),
                 "interface": "harmonic"}

@@ -81,6 +81,9 @@ int RDG_CAT(upload_tab_, RDG_CAT(RDG_TAG, RDG_ORDER))() {
   std::vector<float> xb = gemm::pack_gemm_operand<kN>(*o);
   std::vector<int> gt = gemm::pack_gemm_table<kN>(*o);
   if (xb.size() * 4 != sizeof(g_xb) || gt.size() * 4 != sizeof(g_gtab)) return RDG_EINVAL;
+  // the warp-specialised kernel takes the shared face's rotated-order nodes as constants
+  for (int q = 0; q < kN + 1; ++q)
+    if (gt[3 * kNp + q] != gemm::hyp_of(kN, q)) return RDG_EINVAL;
   if (cudaMemcpyToSymbol(g_xb, xb.data(), sizeof(g_xb)) != cudaSuccess) return RDG_ECUDA;
   if (cudaMemcpyToSymbol(g_gtab, gt.data(), sizeof(g_gtab)) != cudaSuccess) return RDG_ECUDA;
 #endif
