@@ -908,8 +908,10 @@ def run_sweep(args):
 
 def run_orders(args):
     """Graph-replayed SSP-RK3 stage of the circle pulse workload (m x m x 2 triangles) at each
-    order, FP32 and FP64: microseconds per stage, GDOF/s and the stage's algorithmic HBM
-    bytes (stored operators, state in and out, coefficients and ids) per second."""
+    order, FP32 and FP64: microseconds per stage (the default kernel form, and both forms:
+    stage kernel + element kernel, or the one-kernel stage), GDOF/s and the stage's
+    algorithmic HBM bytes (stored operators, state in and out, coefficients and ids) per
+    second."""
     import torch
     import paper_1912_06221_gb300 as rdg
     from synth import circle_pulse
@@ -924,21 +926,27 @@ def run_orders(args):
                 continue
             s = rdg.Solver(w.xy, w.tri, N, w.D_elem, v=w.v, precision=prec)
             u = torch.zeros((s.K, s.Np), dtype=s.dtype, device="cuda")
-            s.set_state(u)
             dt = 1e-9
             per = 32 * 3                          # stages per timed replay (32 steps)
-            for _ in range(max(args.warmup, 1)):
-                s.solve_to_time(0.0, dt, 32)
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(max(args.steps, 1)):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(s.stream)
-                s.solve_to_time(0.0, dt, 32)
-                b.record(s.stream)
+            forms = {}
+            for fname, form in (("two_kernels", rdg.STAGE_TWO_KERNELS), ("one_kernel", rdg.STAGE_ONE_KERNEL),
+                                ("default", rdg.STAGE_AUTO)):
+                s.set_stage_form(form)
+                s.set_state(u)
+                for _ in range(max(args.warmup, 1)):
+                    s.solve_to_time(0.0, dt, 32)
                 torch.cuda.synchronize()
-                ts.append(a.elapsed_time(b) * 1e3 / per)
-            us = float(np.median(ts))
+                ts = []
+                for _ in range(max(args.steps, 1)):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(s.stream)
+                    s.solve_to_time(0.0, dt, 32)
+                    b.record(s.stream)
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b) * 1e3 / per)
+                forms[fname] = float(np.median(ts))
+            us = forms["default"]
+            default_form = "one_kernel" if s.stage_form == rdg.STAGE_ONE_KERNEL else "two_kernels"
             E, K, Np, Nfp = s.E, s.K, s.Np, N + 1
             w_bytes = E * (Nfp * (2 * Np - 1) + 1) * esz
             # the headline's accounting at this order and precision: edge pass (operators, edge
@@ -950,7 +958,9 @@ def run_orders(args):
             alg = alg_bytes_per_element(N, esz) * K
             own = (E * ((Nfp * (2 * Np - 1) + 1) * esz + 8 + Nfp * esz) + 2 * K * Np * esz + K * 5 * esz
                    + int(K * ((3 + 2.0 / 3.0) * Np * esz + 12 + esz) + E * Nfp * esz))
-            rows.append({"N": N, "precision": name, "stage_us": us, "gdofs": s.K * Np / (us * 1e-6) / 1e9,
+            rows.append({"N": N, "precision": name, "stage_us": us, "stage_form": default_form,
+                         "stage_us_two_kernels": forms["two_kernels"], "stage_us_one_kernel": forms["one_kernel"],
+                         "gdofs": s.K * Np / (us * 1e-6) / 1e9,
                          "operator_mb": w_bytes / 1e6, "alg_mb": alg / 1e6, "alg_gbs": alg / (us * 1e-6) / 1e9,
                          "kernels_own_mb": own / 1e6})
             s.synchronize()

@@ -218,6 +218,23 @@ int rdg_rhs_eval_static(rdg_ctx* ctx, const void* u_dev, void* rhs_dev, double t
 enum { RDG_INTEGRATOR_SSP_RK3 = 0, RDG_INTEGRATOR_LSRK54 = 1 };
 int rdg_set_integrator(rdg_ctx* ctx, int integrator);
 
+/* Kernel form of a right-hand-side stage (Algorithm aRDG, Sec. 4.5, and the SSP-RK3 update;
+ * the arithmetic is the same in every form):
+ * RDG_STAGE_TWO_KERNELS  a stage kernel (edge fluxes into the two elements' face slots,
+ *                        volume terms) and an element kernel (LIFT, sources, stage update);
+ * RDG_STAGE_ONE_KERNEL   one element kernel that also computes its three edges' fluxes (each
+ *                        edge's operator read by both of its elements; one launch per stage);
+ * RDG_STAGE_AUTO         (default) the form measured faster for the context's order and
+ *                        precision on GB300 (one kernel for FP32 order 1, two otherwise).
+ * The one-kernel form serves rdg_rhs_eval and SSP-RK3 stages of contexts with stored
+ * operators; the low-storage integrator (which updates its input in place), the GEMM form
+ * and FP32 order 6 (tensor-core volume term) keep two kernels whatever is set.  Errors:
+ * RDG_EINVAL for another value.  rdg_get_stage_form reports the form in use for a
+ * right-hand-side stage (RDG_STAGE_ONE_KERNEL or RDG_STAGE_TWO_KERNELS) in *form. */
+enum { RDG_STAGE_AUTO = 0, RDG_STAGE_TWO_KERNELS = 1, RDG_STAGE_ONE_KERNEL = 2 };
+int rdg_set_stage_form(rdg_ctx* ctx, int form);
+int rdg_get_stage_form(const rdg_ctx* ctx, int* form);
+
 /* One step of the resident state from time t with step dt with the selected integrator;
  * enqueued, no host synchronisation. */
 int rdg_rk_step(rdg_ctx* ctx, double t, double dt);

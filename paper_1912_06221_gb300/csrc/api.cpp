@@ -832,6 +832,19 @@ int enqueue_split_stage(rdg_ctx* ctx, const EdgeArgs<float>& ea, cudaStream_t st
   return rc;
 }
 
+// Whether a right-hand-side stage of this context runs as one kernel (elem_fused_kernel):
+// stored operators, not FP32 order 6 (its volume term runs on the tensor cores beside the
+// edge stream); by default at FP32 order 1 only, the one case where it measured faster on
+// GB300 (circle pulse, 131072 triangles: 5.97 against 7.21 us per stage; order 2 11.36
+// against 10.43, FP64 slower at every order).
+bool one_kernel_stage(const rdg_ctx* ctx) {
+  if (ctx->gemm || (ctx->esz == 4 && split_volume32(ctx->N))) return false;
+  const bool fast = ctx->esz == 4 && ctx->N == 1;
+  const int form = ctx->stage_form == RDG_STAGE_AUTO ? (fast ? RDG_STAGE_ONE_KERNEL : RDG_STAGE_TWO_KERNELS)
+                                                     : ctx->stage_form;
+  return form == RDG_STAGE_ONE_KERNEL;
+}
+
 template <typename T>
 int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta,
                   void* out2 = nullptr, T rka = T(0), T rkb = T(0)) {
@@ -847,6 +860,22 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
   if (prof)
     for (auto& e : ev) e = take_event(ctx);
   int rc;
+  if (mode <= 3 && one_kernel_stage(ctx)) {
+    // one launch: the edge part of the timing is empty
+    if (prof) {
+      cudaEventRecord(ev[0], st);
+      cudaEventRecord(ev[1], st);
+      cudaEventRecord(ev[2], st);
+    }
+    if constexpr (sizeof(T) == 4) rc = launch_fused32(ctx->N, mode, ea, la, st);
+    else rc = launch_fused64(ctx->N, mode, ea, la, st);
+    if (prof) {
+      cudaEventRecord(ev[3], st);
+      ctx->ev_pending[0].push_back({ev[0], ev[1]});
+      ctx->ev_pending[1].push_back({ev[2], ev[3]});
+    }
+    return rc;
+  }
   if (prof) cudaEventRecord(ev[0], st);
   if constexpr (sizeof(T) == 4) {
     if (ctx->gemm) rc = launch_gemm32(ctx->N, ea, st);
@@ -1078,6 +1107,22 @@ int rdg_set_integrator(rdg_ctx* ctx, int integrator) {
   ctx->integrator = integrator;
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   ctx->gexec = nullptr;
+  return RDG_OK;
+}
+
+int rdg_set_stage_form(rdg_ctx* ctx, int form) {
+  if (!ctx) return RDG_EINVAL;
+  if (form != RDG_STAGE_AUTO && form != RDG_STAGE_TWO_KERNELS && form != RDG_STAGE_ONE_KERNEL)
+    return fail(ctx, RDG_EINVAL, "form must be RDG_STAGE_AUTO, RDG_STAGE_TWO_KERNELS or RDG_STAGE_ONE_KERNEL");
+  ctx->stage_form = form;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  return RDG_OK;
+}
+
+int rdg_get_stage_form(const rdg_ctx* ctx, int* form) {
+  if (!ctx || !form) return RDG_EINVAL;
+  *form = one_kernel_stage(ctx) ? RDG_STAGE_ONE_KERNEL : RDG_STAGE_TWO_KERNELS;
   return RDG_OK;
 }
 

@@ -104,6 +104,9 @@ int launch_edge_vol32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 int launch_edge_vol64(int N, const EdgeArgs<double>& a, cudaStream_t s);
 int launch_elem_lite32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s);
 int launch_elem_lite64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s);
+// One-kernel stage (elem_fused_kernel): modes 0..3.
+int launch_fused32(int N, int mode, const EdgeArgs<float>& ea, const ElemArgs<float>& a, cudaStream_t s);
+int launch_fused64(int N, int mode, const EdgeArgs<double>& ea, const ElemArgs<double>& a, cudaStream_t s);
 int upload_elem_tables(int device);
 // GEMM form of the edge flux (FP32 state, tcgen05 split 3xTF32), orders 1..kMaxGemmN: the
 // edge kernel reads per-edge parameter records (EdgeArgs::W) and also computes the volume

@@ -292,17 +292,19 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
   stage_out(a.vol + k0 * NP, sh, nk * NP);
 }
 
-// Edge role of the stage kernel: edge e (one thread per edge), flux_e = W_e [u_k1; u_k2].
-// The gathers hit L2; the operator words are streamed with evict-first 16-byte loads (a warp
-// reads 512 contiguous bytes per load of its tile).
-template <typename T, int N, bool FB>
-__device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
+// Flux of edge e, flux_e = W_e [u_k1; u_k2] (Nfp values in side 1's face order), with its
+// two element ids.  The gathers hit L2; the operator words are streamed with evict-first
+// 16-byte loads (in the stage kernel a warp reads 512 contiguous bytes per load of its tile).
+// Shared by the stage kernel's edge role and the one-kernel stage, so both give the same bits.
+template <typename T, int N>
+__device__ __forceinline__ void edge_acc(const EdgeArgs<T>& a, int64_t e, T (&acc)[nfp_of(N)], int& k1, int& k2) {
   constexpr int NP = np_of(N), NFP = nfp_of(N);
   constexpr int RW = 2 * NP - 1, NWS = NFP * RW + 1;   // stored values per row / per edge
   using V = Vec16<T>;
   using VT = typename V::type;
   constexpr int QW = (NWS + V::n - 1) / V::n;
-  const int k1 = a.k1[e], k2 = a.k2[e];
+  k1 = a.k1[e];
+  k2 = a.k2[e];
   T u1[NP], u2[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) u1[j] = u2[j] = T(0);
@@ -340,7 +342,6 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
   const VT* w = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
   const bool keep = (e >> 5) < a.keep_tiles;
   const uint64_t pol = keep ? l2_keep_policy() : 0;
-  T acc[NFP];
 #pragma unroll
   for (int r = 0; r < NFP; ++r) acc[r] = T(0);
   T srow = T(0);
@@ -360,6 +361,16 @@ __device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
   }
 #pragma unroll
   for (int r = 0; r < NFP; ++r) acc[r] = fma(srow, ub, acc[r]);
+}
+
+// Edge role of the stage kernel: edge e (one thread per edge), its flux scattered to the two
+// elements' face slots (FB) or written to the edge's row of a.flux.
+template <typename T, int N, bool FB>
+__device__ __noinline__ void stage_edge(const EdgeArgs<T>& a, int64_t e) {
+  constexpr int NFP = nfp_of(N);
+  T acc[NFP];
+  int k1, k2;
+  edge_acc<T, N>(a, e, acc, k1, k2);
   if constexpr (FB) {
     // scatter to the two elements' face slots: side 1 in its face order, side 2 (outward
     // normal -n1, face traversed the other way) negated and reversed
@@ -633,6 +644,99 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
   }
 }
 
+// One-kernel stage for low orders: thread = element.  Each element computes the fluxes of its
+// three edges itself (edge_acc, the same arithmetic as the stage kernel's edge role, so an
+// edge's two elements use bitwise the same flux and the scheme stays conservative), then its
+// volume term, LIFT, sources and the stage.  An edge's operator is read by both of its
+// elements (the second read mostly hits L2: elements are ordered along a space-filling
+// curve); in exchange the stage is one launch with no face-flux or volume-term round trip,
+// which pays where a stage's work is small against a launch.  Everything it reads may be
+// written by the previous stage, so it waits for the predecessor first.  Modes 0..3 only: its
+// output must not be a buffer that other blocks gather from (the low-storage stage updates its
+// input in place, so it keeps the two-kernel form).
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kElemBlock) elem_fused_kernel(EdgeArgs<T> ea, ElemArgs<T> a) {
+  static_assert(MODE >= 0 && MODE <= 3, "SSP-RK3 stages and the right-hand side only");
+  constexpr int NP = np_of(N), NFP = nfp_of(N);
+  constexpr int OLIFT = 4 * NP * NP;
+  constexpr int BLK = kElemBlock;
+  constexpr bool NEED_UN = MODE == 2 || MODE == 3;
+  __shared__ __align__(16) T shs[BLK * NP];
+  __shared__ __align__(16) T shn[NEED_UN ? BLK * NP : 4];
+  __shared__ T tau_s[RDG_MAX_FORCING_TERMS];
+  const int64_t k0 = (int64_t)blockIdx.x * BLK;
+  const int nk = (int)min((int64_t)BLK, a.K - k0);
+  const int tid = threadIdx.x;
+  const bool active = tid < nk;
+  const int64_t k = active ? k0 + tid : k0;
+  wait_for_predecessor();
+  allow_dependents();
+  {
+    Staged<T, BLK, NP> gs, gn;
+    gs.load(a.us + k0 * NP, nk * NP);
+    if (NEED_UN) gn.load(a.un + k0 * NP, nk * NP);
+    gs.store(shs, nk * NP);
+    if (NEED_UN) gn.store(shn, nk * NP);
+  }
+  if (tid < a.frc.nsrc) tau_s[tid] = (T)tau_of(a.frc.kind[tid], a.frc.omega[tid], stage_time(a.time));
+  __syncthreads();
+  T rhs[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) rhs[i] = T(0);
+  if (active) {
+    T u[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) u[j] = shs[tid * NP + j];
+    if (ea.Dn)
+      volume_row<T, N, true>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k],
+                             rhs, ea.Dn + k * NP);
+    else
+      volume_row<T, N>(u, a.geo[k], a.geo[a.K + k], a.geo[2 * a.K + k], a.geo[3 * a.K + k], a.geo[4 * a.K + k], rhs);
+    const T ij = a.geo[5 * a.K + k];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      int er = a.eref[(int64_t)f * a.K + k];
+      if (er < 0 || (er >> 1) >= a.E) {     // self-check: record and use edge 0 instead
+        report(a.err, kErrBadIndex);
+        er = 0;
+      }
+      T acc[NFP], q[NFP];
+      int k1, k2;
+      edge_acc<T, N>(ea, er >> 1, acc, k1, k2);
+      // side 1 in its face order; side 2 (outward normal -n1, face traversed the other way)
+      // negated and reversed
+#pragma unroll
+      for (int c = 0; c < NFP; ++c) q[c] = (er & 1) ? -acc[NFP - 1 - c] : acc[c];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < NFP; ++c) s = fma((T)RDG_TAB[OLIFT + i * 3 * NFP + f * NFP + c], q[c], s);
+        rhs[i] -= ij * s;
+      }
+    }
+    for (int m = 0; m < a.frc.nsrc; ++m) {
+      const T* S = a.S + ((int64_t)m * a.K + k) * NP;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) rhs[i] = fma(tau_s[m], S[i], rhs[i]);
+    }
+  }
+  {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      if (MODE >= 1) rhs[i] = fma(a.dt, rhs[i], shs[tid * NP + i]);
+      if (MODE >= 2) rhs[i] = rk_combine<T, MODE>(shn[tid * NP + i], rhs[i]);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) shs[tid * NP + i] = rhs[i];
+    }
+    __syncthreads();
+    stage_out(a.out + k0 * NP, shs, nk * NP);
+  }
+}
+
 }  // namespace dev
 
 // Host-side launch helpers instantiated by the including translation unit.
@@ -681,6 +785,20 @@ inline int launch_edge_fb_t(const EdgeArgs<T>& a, cudaStream_t s) {
   if (a.E == 0) return RDG_OK;
   const int64_t ge = (a.E + kStageBlock - 1) / kStageBlock;
   return launch_pdl(dev::edge_flux_kernel<T, N, 2>, (unsigned)ge, kStageBlock, s, a);
+}
+
+// One-kernel stage (elem_fused_kernel), programmatic launch.
+template <typename T, int N>
+inline int launch_fused_t(int mode, const EdgeArgs<T>& ea, const ElemArgs<T>& a, cudaStream_t s) {
+  if (a.K == 0) return RDG_OK;
+  const unsigned g = (unsigned)((a.K + kElemBlock - 1) / kElemBlock);
+  switch (mode) {
+    case 0: return launch_pdl(dev::elem_fused_kernel<T, N, 0>, g, kElemBlock, s, ea, a);
+    case 1: return launch_pdl(dev::elem_fused_kernel<T, N, 1>, g, kElemBlock, s, ea, a);
+    case 2: return launch_pdl(dev::elem_fused_kernel<T, N, 2>, g, kElemBlock, s, ea, a);
+    case 3: return launch_pdl(dev::elem_fused_kernel<T, N, 3>, g, kElemBlock, s, ea, a);
+    default: return RDG_EINVAL;   // the low-storage stage updates its input in place
+  }
 }
 
 template <typename T, int N, bool VOLIN = false>

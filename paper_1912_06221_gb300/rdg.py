@@ -21,6 +21,7 @@ FP64, FP32, FP32_3XTF32 = 0, 1, 2
 TAU_CONST, TAU_COS, TAU_SIN = 0, 1, 2
 IFACE_ALG2, IFACE_HARMONIC, IFACE_ALG1 = 0, 1, 2
 SSP_RK3, LSRK54 = 0, 1
+STAGE_AUTO, STAGE_TWO_KERNELS, STAGE_ONE_KERNEL = 0, 1, 2
 BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 ERR_NAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ERANK", -6: "ETIMEOUT", -7: "ESTATE"}
 
@@ -62,6 +63,8 @@ SIGNATURES = {
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
     "rdg_get_edge_operators": (_INT, [_P, _P, _P]),
     "rdg_set_integrator": (_INT, [_P, _INT]),
+    "rdg_set_stage_form": (_INT, [_P, _INT]),
+    "rdg_get_stage_form": (_INT, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rdg_error_quadrature": (_INT, [_P, ctypes.POINTER(_INT), _P]),
     "rdg_error_norms": (_INT, [_P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rdg_peak_fma": (_INT, [_INT, _INT, ctypes.POINTER(_D)]),
@@ -307,6 +310,17 @@ class Solver:
     def set_integrator(self, kind: int):
         """SSP_RK3 (default) or LSRK54 (the paper's five-stage fourth-order scheme)."""
         self._call("rdg_set_integrator", int(kind))
+
+    def set_stage_form(self, form: int):
+        """STAGE_AUTO (default), STAGE_TWO_KERNELS or STAGE_ONE_KERNEL (rdg_set_stage_form)."""
+        self._call("rdg_set_stage_form", int(form))
+
+    @property
+    def stage_form(self) -> int:
+        """The kernel form a right-hand-side stage uses (STAGE_ONE_KERNEL or STAGE_TWO_KERNELS)."""
+        f = ctypes.c_int(0)
+        self._call("rdg_get_stage_form", ctypes.byref(f))
+        return f.value
 
     def solve_to_time(self, t0: float, dt: float, nsteps: int):
         self._call("rdg_solve_to_time", float(t0), float(dt), int(nsteps))
