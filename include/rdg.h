@@ -246,6 +246,24 @@ int rdg_rk_step(rdg_ctx* ctx, double t, double dt);
  * before each stage.  Errors: RDG_ESTATE, RDG_EINVAL (stage out of range, bad dt). */
 int rdg_rk_stage(rdg_ctx* ctx, int stage, double t, double dt);
 
+/* The same stage in two parts, so that a split mesh's halo exchange overlaps the work that
+ * does not need it (the per-stage exchange of the partitioned Algorithm aRDG, Sec. 4.5: an
+ * edge reads all 2 Np values of both neighbours).  Part 0 enqueues the edges with no halo
+ * side (the first e_split edges of a partitioned upload; e_split is a multiple of 32) and the
+ * owned elements' volume terms: it reads owned rows of the stage input only.  Part 1 enqueues
+ * the remaining edges and the element update; the caller writes the halo rows of
+ * rdg_stage_buffer(stage) between the two (rdg_rows_scatter).  Parts 0 then 1 give the same
+ * owned rows as rdg_rk_stage (halo rows of the stage output are not defined).  Contexts that
+ * cannot split a stage (not partitioned, the GEMM form, FP32 order 6, the one-kernel form)
+ * run the whole stage in part 1 and nothing in part 0.  Errors: as rdg_rk_stage, RDG_EINVAL
+ * for a part other than 0 or 1. */
+int rdg_rk_stage_part(rdg_ctx* ctx, int stage, int part, double t, double dt);
+
+/* Owned elements and e_split (edges [0, e_split) touch no halo element) of the uploaded
+ * mesh: n_owned = nt and e_split = the edge count for an unsplit upload.  Errors:
+ * RDG_ESTATE before a mesh upload. */
+int rdg_split_counts(const rdg_ctx* ctx, int64_t* n_owned, int64_t* e_split);
+
 /* Device pointer of the input buffer [nt][Np] of stage `stage` (SSP-RK3: the state, then the
  * two stage buffers; the low-storage scheme: the state for every stage), owned by the context
  * and valid until the next rdg_operator_setup or rdg_destroy. */

@@ -382,6 +382,23 @@ static int mesh_upload_impl(rdg_ctx* ctx, int64_t nv, const double* xy, int64_t 
   ctx->edges.insert(ctx->edges.end(), bnd.begin(), bnd.end());
   ctx->E = (int64_t)ctx->edges.size();
   ctx->B = (int64_t)bnd.size();
+  ctx->e_split = ctx->E;
+  if (n_owned < nt) {
+    // a split mesh: first a multiple of 32 (whole operator tiles) of the edges with no halo
+    // side, which a stage may process while the halo rows are still in flight, then the rest
+    // (order otherwise kept)
+    auto no_halo = [&](const EdgeRec& r) { return r.k1 < n_owned && r.k2 < n_owned; };
+    std::vector<EdgeRec> a, rest;
+    for (const EdgeRec& r : ctx->edges) (no_halo(r) ? a : rest).push_back(r);
+    ctx->e_split = (int64_t)a.size() / kTile * kTile;
+    rest.insert(rest.begin(), a.begin() + ctx->e_split, a.end());
+    a.resize(ctx->e_split);
+    a.insert(a.end(), rest.begin(), rest.end());
+    ctx->edges.swap(a);
+  }
+  ctx->bedge.assign(ctx->B, -1);
+  for (int64_t e = 0; e < ctx->E; ++e)
+    if (ctx->edges[e].k2 < 0) ctx->bedge[-1 - (int64_t)ctx->edges[e].k2] = e;
   ctx->eref.assign(3 * nt, -1);
   for (int64_t e = 0; e < ctx->E; ++e) {
     const EdgeRec& r = ctx->edges[e];
@@ -693,7 +710,7 @@ int rdg_get_ghost_coords(rdg_ctx* ctx, double* xy) {
   const RefOps* o = get_refops(ctx->N, nullptr);
   const int kc[3] = {2, 0, 1};
   for (int64_t b = 0; b < ctx->B; ++b) {
-    const EdgeRec& r = ctx->edges[ctx->E - ctx->B + b];
+    const EdgeRec& r = ctx->edges[ctx->bedge[b]];
     const double* p = &ctx->exy[6 * r.k1];
     double e1x = p[2 * kFaceA[r.f1]], e1y = p[2 * kFaceA[r.f1] + 1];
     double e2x = p[2 * kFaceB[r.f1]], e2y = p[2 * kFaceB[r.f1] + 1];
@@ -845,17 +862,56 @@ bool one_kernel_stage(const rdg_ctx* ctx) {
   return form == RDG_STAGE_ONE_KERNEL;
 }
 
+// Whether a stage of this context can run in two parts around a halo exchange (the stage
+// kernel and element kernel form on a split mesh).
+bool splittable_stage(const rdg_ctx* ctx, int mode) {
+  return ctx->n_owned < ctx->K && !ctx->gemm && !(ctx->esz == 4 && split_volume32(ctx->N)) &&
+         !(mode <= 3 && one_kernel_stage(ctx));
+}
+
+// part -1: the whole stage.  On a split mesh, part 0: the edges with no halo side and the owned
+// elements' volume terms (they read owned rows only); part 1: the remaining edges and the
+// element update.  A stage that cannot be split runs whole in part 1 (part 0 enqueues nothing).
 template <typename T>
 int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int mode, T dt, const TimeArg& ta,
-                  void* out2 = nullptr, T rka = T(0), T rkb = T(0)) {
+                  void* out2 = nullptr, T rka = T(0), T rkb = T(0), int part = -1) {
   EdgeArgs<T> ea{ctx->d_k1, ctx->d_k2, ctx->d_W, (const T*)us, (T*)ctx->d_flux, (const T*)ctx->d_G,
                  ctx->E, ctx->B, ctx->frc, ta, ctx->d_err, ctx->K, (T*)ctx->d_vol,
                  (const T*)ctx->d_geo, ctx->d_f12, (T*)ctx->d_fb, keep_tiles(ctx), (const T*)ctx->d_Dn};
   ElemArgs<T> la{(const T*)us, (const T*)un, (T*)out, (const T*)ctx->d_flux, ctx->d_eref, (const T*)ctx->d_geo,
                  (const T*)ctx->d_S, ctx->K, dt, ctx->frc, ta, ctx->d_err, ctx->E, (const T*)ctx->d_vol,
                  (const T*)ctx->d_fb, (T*)out2, rka, rkb};
-  const bool prof = ctx->prof && !ctx->capturing;
   cudaStream_t st = ls(ctx);
+  if (part >= 0 && splittable_stage(ctx, mode)) {
+    int rc = RDG_OK;
+    if (part == 0) {
+      if (ctx->n_owned == 0) return RDG_OK;
+      EdgeArgs<T> e0 = ea;
+      e0.E = ctx->e_split;
+      e0.Kvol = ctx->n_owned;
+      if constexpr (sizeof(T) == 4) rc = launch_edge_vol32(ctx->N, e0, st);
+      else rc = launch_edge_vol64(ctx->N, e0, st);
+      return rc;
+    }
+    EdgeArgs<T> e1 = ea;
+    const int64_t t0 = ctx->e_split / kTile;
+    const int64_t tile_bytes = (int64_t)w_vecs_per_edge(ctx->N, ctx->esz) * kTile * 16;
+    e1.k1 = ctx->d_k1 + ctx->e_split;
+    e1.k2 = ctx->d_k2 + ctx->e_split;
+    e1.f12 = ctx->d_f12 + ctx->e_split;
+    e1.W = static_cast<const char*>(ctx->d_W) + t0 * tile_bytes;
+    e1.E = ctx->E - ctx->e_split;
+    e1.keep_tiles = std::max<int64_t>(0, ea.keep_tiles - t0);
+    if constexpr (sizeof(T) == 4) rc = launch_edge_only32(ctx->N, e1, st);
+    else rc = launch_edge_only64(ctx->N, e1, st);
+    if (rc == RDG_OK) {
+      if constexpr (sizeof(T) == 4) rc = launch_elem_lite32(ctx->N, mode, la, st);
+      else rc = launch_elem_lite64(ctx->N, mode, la, st);
+    }
+    return rc;
+  }
+  if (part == 0) return RDG_OK;
+  const bool prof = ctx->prof && !ctx->capturing;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   if (prof)
     for (auto& e : ev) e = take_event(ctx);
@@ -952,22 +1008,23 @@ void* stage_input(rdg_ctx* ctx, int stage) {
 
 // One stage of the selected integrator, the same launches as the stage inside
 // enqueue_rk_step (time offsets in units of dt from the step start in base).
-int enqueue_one_stage(rdg_ctx* ctx, int stage, const TimeArg& base, double dt) {
+int enqueue_one_stage(rdg_ctx* ctx, int stage, const TimeArg& base, double dt, int part = -1) {
   TimeArg ts = base;
   if (ctx->integrator == RDG_INTEGRATOR_LSRK54) {
     ts.off = base.off + kLsrkC[stage];
     if (ctx->esz == 4)
       return enqueue_stage<float>(ctx, ctx->d_u, ctx->d_u1, ctx->d_u, 4, (float)dt, ts, ctx->d_u1, (float)kLsrkA[stage],
-                                  (float)kLsrkB[stage]);
-    return enqueue_stage<double>(ctx, ctx->d_u, ctx->d_u1, ctx->d_u, 4, dt, ts, ctx->d_u1, kLsrkA[stage], kLsrkB[stage]);
+                                  (float)kLsrkB[stage], part);
+    return enqueue_stage<double>(ctx, ctx->d_u, ctx->d_u1, ctx->d_u, 4, dt, ts, ctx->d_u1, kLsrkA[stage], kLsrkB[stage],
+                                 part);
   }
   static const double off[3] = {0.0, 1.0, 0.5};
   ts.off = base.off + off[stage];
   void* in = stage_input(ctx, stage);
   void* out = stage == 0 ? ctx->d_u1 : (stage == 1 ? ctx->d_u2 : ctx->d_u);
   const void* un = stage == 0 ? nullptr : ctx->d_u;
-  if (ctx->esz == 4) return enqueue_stage<float>(ctx, in, un, out, stage + 1, (float)dt, ts);
-  return enqueue_stage<double>(ctx, in, un, out, stage + 1, dt, ts);
+  if (ctx->esz == 4) return enqueue_stage<float>(ctx, in, un, out, stage + 1, (float)dt, ts, nullptr, 0.0f, 0.0f, part);
+  return enqueue_stage<double>(ctx, in, un, out, stage + 1, dt, ts, nullptr, 0.0, 0.0, part);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -1024,6 +1081,26 @@ int rdg_rk_stage(rdg_ctx* ctx, int stage, double t, double dt) {
   TimeArg ta{nullptr, t, dt, 0.0};
   int rc = enqueue_one_stage(ctx, stage, ta, dt);
   return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_rk_stage_part(rdg_ctx* ctx, int stage, int part, double t, double dt) {
+  if (!ctx) return RDG_EINVAL;
+  if (!ctx->ops_ok) return fail(ctx, RDG_ESTATE, "rdg_operator_setup must come first");
+  if (!(dt > 0) || !std::isfinite(t)) return fail(ctx, RDG_EINVAL, "dt must be positive and t finite");
+  const int nst = ctx->integrator == RDG_INTEGRATOR_LSRK54 ? 5 : 3;
+  if (stage < 0 || stage >= nst) return fail(ctx, RDG_EINVAL, "stage out of range for the integrator");
+  if (part != 0 && part != 1) return fail(ctx, RDG_EINVAL, "part must be 0 or 1");
+  DeviceGuard g(ctx->device);
+  TimeArg ta{nullptr, t, dt, 0.0};
+  int rc = enqueue_one_stage(ctx, stage, ta, dt, part);
+  return rc == RDG_OK ? RDG_OK : fail(ctx, rc, "kernel launch failed");
+}
+
+int rdg_split_counts(const rdg_ctx* ctx, int64_t* n_owned, int64_t* e_split) {
+  if (!ctx || !ctx->mesh_ok) return RDG_ESTATE;
+  if (n_owned) *n_owned = ctx->n_owned;
+  if (e_split) *e_split = ctx->e_split;
+  return RDG_OK;
 }
 
 int rdg_stage_buffer(rdg_ctx* ctx, int stage, void** dev_ptr) {

@@ -31,7 +31,10 @@ struct rdg_ctx {
   int64_t n_owned = 0;            // elements [n_owned, K) are halo copies (partitioned upload)
   int bc = 0;
   std::vector<double> exy;       // [K][6]
-  std::vector<EdgeRec> edges;    // interior edges first, then boundary edges
+  std::vector<EdgeRec> edges;    // interior edges first, then boundary edges (a split mesh:
+                                 // first the e_split edges with no halo side)
+  std::vector<int64_t> bedge;    // edge of ghost b (boundary edge b)
+  int64_t e_split = 0;           // edges [0, e_split) touch no halo element (a multiple of 32)
   std::vector<int32_t> eref;     // [3][K]
   // operators
   bool ops_ok = false;

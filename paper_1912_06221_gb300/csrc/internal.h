@@ -64,6 +64,7 @@ struct EdgeArgs {
   T* fb;               // fused form: face fluxes [K][3][Nfp] in each element's own face order
   int64_t keep_tiles;  // operator tiles [0, keep_tiles) are loaded evict-last (kept in L2)
   const T* Dn;         // D at the nodes [K][Np] when given so (geo then holds the metric alone), else null
+  int64_t Kvol;        // fused form: volume terms of elements [0, Kvol) only (0: all K)
 };
 
 // Device error bits reported through rdg_synchronize.
@@ -118,6 +119,9 @@ int launch_gemm32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 bool split_volume32(int N);
 int launch_volume32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 int launch_edge_fb32(int N, const EdgeArgs<float>& a, cudaStream_t s);
+// Edge blocks only (fluxes into the face slots), every order and precision.
+int launch_edge_only32(int N, const EdgeArgs<float>& a, cudaStream_t s);
+int launch_edge_only64(int N, const EdgeArgs<double>& a, cudaStream_t s);
 int gemm_param_words(int N);   // 16-byte words of an edge's parameter record
 
 // ---- setup (FP64) -------------------------------------------------------------------

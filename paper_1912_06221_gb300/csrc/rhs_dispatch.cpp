@@ -9,7 +9,8 @@ namespace rdg {
   int launch_elem_##tag##n(int mode, const ElemArgs<T>& a, cudaStream_t s);     \
   int launch_edge_vol_##tag##n(const EdgeArgs<T>& a, cudaStream_t s);           \
   int launch_elem_lite_##tag##n(int mode, const ElemArgs<T>& a, cudaStream_t s); \
-  int launch_fused_##tag##n(int mode, const EdgeArgs<T>& ea, const ElemArgs<T>& a, cudaStream_t s);
+  int launch_fused_##tag##n(int mode, const EdgeArgs<T>& ea, const ElemArgs<T>& a, cudaStream_t s); \
+  int launch_edge_only_##tag##n(const EdgeArgs<T>& a, cudaStream_t s);
 #define RDG_DECL_ALL(tag, T) \
   RDG_DECL(tag, T, 1) RDG_DECL(tag, T, 2) RDG_DECL(tag, T, 3) RDG_DECL(tag, T, 4) RDG_DECL(tag, T, 5) RDG_DECL(tag, T, 6)
 RDG_DECL_ALL(f, float)
@@ -31,6 +32,7 @@ RDG_DECL_ALL(d, double)
 #define CALL_EDGE_VOL(tag, n) launch_edge_vol_##tag##n(a, s)
 #define CALL_ELEM_LITE(tag, n) launch_elem_lite_##tag##n(mode, a, s)
 #define CALL_FUSED(tag, n) launch_fused_##tag##n(mode, ea, a, s)
+#define CALL_EDGE_ONLY(tag, n) launch_edge_only_##tag##n(a, s)
 
 int launch_edge32(int N, const EdgeArgs<float>& a, cudaStream_t s) { RDG_SWITCH(f, CALL_EDGE) }
 int launch_edge64(int N, const EdgeArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_EDGE) }
@@ -40,6 +42,8 @@ int launch_edge_vol32(int N, const EdgeArgs<float>& a, cudaStream_t s) { RDG_SWI
 int launch_edge_vol64(int N, const EdgeArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_EDGE_VOL) }
 int launch_elem_lite32(int N, int mode, const ElemArgs<float>& a, cudaStream_t s) { RDG_SWITCH(f, CALL_ELEM_LITE) }
 int launch_elem_lite64(int N, int mode, const ElemArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_ELEM_LITE) }
+int launch_edge_only32(int N, const EdgeArgs<float>& a, cudaStream_t s) { RDG_SWITCH(f, CALL_EDGE_ONLY) }
+int launch_edge_only64(int N, const EdgeArgs<double>& a, cudaStream_t s) { RDG_SWITCH(d, CALL_EDGE_ONLY) }
 int launch_fused32(int N, int mode, const EdgeArgs<float>& ea, const ElemArgs<float>& a, cudaStream_t s) {
   RDG_SWITCH(f, CALL_FUSED)
 }

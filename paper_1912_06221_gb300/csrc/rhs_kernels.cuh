@@ -260,7 +260,7 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
   __shared__ __align__(16) T tab[SMEM_TAB ? VolTab<T, N>::SIZE : 4];
   const int tid = threadIdx.x;
   const int64_t k0 = v * kStageBlock;
-  const int nk = (int)min((int64_t)kStageBlock, a.K - k0);
+  const int nk = (int)min((int64_t)kStageBlock, (a.Kvol > 0 ? a.Kvol : a.K) - k0);
   {
     Staged<T, kStageBlock, NP> g;
     g.load(a.u + k0 * NP, nk * NP);
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kStageBlock, stage_min_blocks<T, N, KIND>()) e
   if constexpr (KIND == 1) {
     __shared__ __align__(16) T sh[kStageBlock * NP];
     const int64_t nb = gridDim.x;
-    const int64_t nv = (a.K + kStageBlock - 1) / kStageBlock;
+    const int64_t nv = ((a.Kvol > 0 ? a.Kvol : a.K) + kStageBlock - 1) / kStageBlock;
     const int64_t b = blockIdx.x;
     const int64_t v0 = (b * nv) / nb, v1 = ((b + 1) * nv) / nb;
     if (v1 > v0) {
@@ -772,8 +772,9 @@ inline int sm_count() {
 
 template <typename T, int N, bool VOL = false>
 inline int launch_edge_t(const EdgeArgs<T>& a, cudaStream_t s) {
-  if (a.E == 0 && (!VOL || a.K == 0)) return RDG_OK;
-  const int64_t ge = (a.E + kStageBlock - 1) / kStageBlock, gv = (a.K + kStageBlock - 1) / kStageBlock;
+  const int64_t kv = a.Kvol > 0 ? a.Kvol : a.K;
+  if (a.E == 0 && (!VOL || kv == 0)) return RDG_OK;
+  const int64_t ge = (a.E + kStageBlock - 1) / kStageBlock, gv = (kv + kStageBlock - 1) / kStageBlock;
   if constexpr (VOL) return launch_pdl(dev::edge_flux_kernel<T, N, 1>, (unsigned)(ge + gv), kStageBlock, s, a);
   dev::edge_flux_kernel<T, N, 0><<<(unsigned)ge, kStageBlock, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? RDG_OK : RDG_ECUDA;

@@ -138,6 +138,10 @@ int RDG_CAT(launch_elem_lite_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const Elem
   return launch_elem_t<RDG_REAL, kN, true>(mode, a, s);
 }
 
+int RDG_CAT(launch_edge_only_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_REAL>& a, cudaStream_t s) {
+  return launch_edge_fb_t<RDG_REAL, kN>(a, s);
+}
+
 int RDG_CAT(launch_fused_, RDG_CAT(RDG_TAG, RDG_ORDER))(int mode, const EdgeArgs<RDG_REAL>& ea,
                                                       const ElemArgs<RDG_REAL>& a, cudaStream_t s) {
   return launch_fused_t<RDG_REAL, kN>(mode, ea, a, s);

@@ -9,11 +9,14 @@ owning rank), uploads it with rdg_mesh_upload_partition, and before every stage 
 rows its neighbours hold as halo and receives its own halo rows (one grouped send/receive per
 neighbour per stage, NCCL over torch.distributed on GPUs, gloo on CPUs).  Each rank computes
 every local row; the owned rows are exact because the halo rows hold the owners' values.
+The exchange overlaps the part of the stage that reads owned rows only (the edges with no
+halo side, which the partitioned upload puts first, and the owned volume terms).
 
 Host logic only: the partition (recursive coordinate bisection of element centroids), face
 adjacency (vertex ids, then midpoints modulo the period, as the library's mesh upload
 matches faces) and the send/receive plan.  The gathers and scatters of rows and every stage
-run in the library's kernels (rdg_rows_gather, rdg_rows_scatter, rdg_rk_stage).
+run in the library's kernels (rdg_rows_gather, rdg_rows_scatter, rdg_rk_stage,
+rdg_rk_stage_part).
 """
 from __future__ import annotations
 
@@ -183,11 +186,36 @@ class SplitSolver:
         halo_exchange(self.plan, dist, self.send_bufs, self.recv_bufs,
                       lambda p, b: self.pack(dst, p, b), lambda p, b: self.unpack(dst, p, b), group)
 
-    def rk_step(self, t: float, dt: float, dist, group=None, stages: int = 3):
-        """One step: before each stage the stage input's halo rows are refreshed."""
+    def exchange_begin(self, dst: int, dist, group=None):
+        """Pack the rows every neighbour needs from the local array at dst and post the grouped
+        send/receive; returns the requests (on NCCL the transfers run on NCCL's stream)."""
+        for p in self.plan.peers:
+            self.pack(dst, p, self.send_bufs[p])
+        ops = [dist.P2POp(dist.isend, self.send_bufs[p], p, group) for p in self.plan.peers]
+        ops += [dist.P2POp(dist.irecv, self.recv_bufs[p], p, group) for p in self.plan.peers]
+        return dist.batch_isend_irecv(ops) if ops else []
+
+    def exchange_end(self, reqs, dst: int):
+        """Wait for the requests (the solver's stream waits for NCCL) and store the halo rows."""
+        for r in reqs:
+            r.wait()
+        for p in self.plan.peers:
+            self.unpack(dst, p, self.recv_bufs[p])
+
+    def rk_step(self, t: float, dt: float, dist, group=None, stages: int = 3, overlap: bool = True):
+        """One step.  overlap: each stage's exchange runs while the edges with no halo side
+        and the owned volume terms are computed (rdg_rk_stage_part 0), the rest after it
+        (part 1); otherwise the halo rows are refreshed before each whole stage."""
         for st in range(stages):
-            self.exchange(self.s.stage_buffer(st), dist, group)
-            self.s.rk_stage(st, t, dt)
+            buf = self.s.stage_buffer(st)
+            if overlap:
+                reqs = self.exchange_begin(buf, dist, group)
+                self.s.rk_stage_part(st, 0, t, dt)
+                self.exchange_end(reqs, buf)
+                self.s.rk_stage_part(st, 1, t, dt)
+            else:
+                self.exchange(buf, dist, group)
+                self.s.rk_stage(st, t, dt)
 
     def set_owned_state(self, u_global):
         """Resident state from a global [K_global, Np] array (owned and halo rows)."""

@@ -63,6 +63,8 @@ SIGNATURES = {
     "rdg_reference_operator": (_INT, [_INT, _INT, _P]),
     "rdg_get_edge_operators": (_INT, [_P, _P, _P]),
     "rdg_set_integrator": (_INT, [_P, _INT]),
+    "rdg_rk_stage_part": (_INT, [_P, _INT, _INT, _D, _D]),
+    "rdg_split_counts": (_INT, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "rdg_set_stage_form": (_INT, [_P, _INT]),
     "rdg_get_stage_form": (_INT, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rdg_error_quadrature": (_INT, [_P, ctypes.POINTER(_INT), _P]),
@@ -292,6 +294,16 @@ class Solver:
     def rk_stage(self, stage: int, t: float, dt: float):
         """One stage of a step from step start t (rdg_rk_stage)."""
         self._call("rdg_rk_stage", int(stage), float(t), float(dt))
+
+    def rk_stage_part(self, stage: int, part: int, t: float, dt: float):
+        """Part 0 or 1 of a stage, around a halo exchange (rdg_rk_stage_part)."""
+        self._call("rdg_rk_stage_part", int(stage), int(part), float(t), float(dt))
+
+    def split_counts(self):
+        """(owned elements, e_split): edges [0, e_split) touch no halo element."""
+        n, e = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._call("rdg_split_counts", ctypes.byref(n), ctypes.byref(e))
+        return n.value, e.value
 
     def stage_buffer(self, stage: int) -> int:
         """Device address of the input buffer of `stage` (rdg_stage_buffer)."""

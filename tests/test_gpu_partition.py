@@ -6,7 +6,10 @@ per part on the same GPU, and the transport between them (NCCL point-to-point be
 replaced by device-to-device copies of the packed halo rows, made before every stage in
 the order a grouped send/receive would.  No kernel of one part waits on another part's
 kernel.  The owned rows after ten split SSP-RK3 steps equal the unsplit oracle's (FP64
-1e-10, FP32 1e-5, normwise and element by element) and the unsplit library run's."""
+1e-10, FP32 1e-5, normwise and element by element) and the unsplit library run's, with each
+stage run whole after the exchange or in two parts around it (rdg_rk_stage_part: the edges
+with no halo side and the owned volume terms before the exchange, the rest after); the
+partitioned upload puts a multiple of 32 halo-free edges first."""
 import numpy as np
 import pytest
 
@@ -49,8 +52,12 @@ def _exchange_all(parts, stage):
 @pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
 @pytest.mark.parametrize("bc", [rdg.BC_PERIODIC, rdg.BC_DIRICHLET])
-def test_split_mesh_steps_equal_unsplit(world, prec, bc):
-    N, m, v = 3, 10, (0.7, -0.4)
+@pytest.mark.parametrize("overlap", [False, True])
+@pytest.mark.parametrize("N", [3, 6])
+def test_split_mesh_steps_equal_unsplit(world, prec, bc, overlap, N):
+    if N == 6 and (world == 3 or bc == rdg.BC_DIRICHLET):
+        pytest.skip("order 6 (FP32: a stage that runs whole in part 1) once per precision")
+    m, v = (16, (0.7, -0.4)) if N == 3 else (8, (0.7, -0.4))
     xy, tri = unit_square_mesh(m, 0.1, 6)
     K = tri.shape[0]
     c = xy[tri].mean(axis=1)
@@ -70,11 +77,27 @@ def test_split_mesh_steps_equal_unsplit(world, prec, bc):
     me = Mesh(xy, tri, N, bc=bc)
     pr = Problem(me, D, v=v, interface="alg1", ghost_fn=(lambda x, y, t: 0.0 * x) if bc == rdg.BC_DIRICHLET else None)
     dt, nsteps = stable_dt(pr, 0.5, 20), 10
+    for sp in parts:
+        n_owned, e_split = sp.s.split_counts()
+        assert n_owned == sp.n_owned and e_split % 32 == 0
+        _, ids = sp.s.edge_operators()
+        k1, k2 = ids[:e_split, 0], ids[:e_split, 2]
+        assert (k1 < n_owned).all() and (k2 < n_owned).all()
+        assert (np.maximum(ids[e_split:, 0], ids[e_split:, 2]) >= n_owned).sum() > 0
+        if N == 3:
+            assert e_split > 0
     for n in range(nsteps):
         for st in range(3):
-            _exchange_all(parts, st)
-            for sp in parts:
-                sp.s.rk_stage(st, n * dt, dt)
+            if overlap:
+                for sp in parts:
+                    sp.s.rk_stage_part(st, 0, n * dt, dt)
+                _exchange_all(parts, st)
+                for sp in parts:
+                    sp.s.rk_stage_part(st, 1, n * dt, dt)
+            else:
+                _exchange_all(parts, st)
+                for sp in parts:
+                    sp.s.rk_stage(st, n * dt, dt)
     whole.solve_to_time(0.0, dt, nsteps)
     got = np.zeros((K, whole.Np))
     for sp in parts:
