@@ -852,8 +852,8 @@ int enqueue_split_stage(rdg_ctx* ctx, const EdgeArgs<float>& ea, cudaStream_t st
 // Whether a right-hand-side stage of this context runs as one kernel (elem_fused_kernel):
 // stored operators, not FP32 order 6 (its volume term runs on the tensor cores beside the
 // edge stream); by default at FP32 order 1 only, the one case where it measured faster on
-// GB300 (circle pulse, 131072 triangles: 5.97 against 7.21 us per stage; order 2 11.36
-// against 10.43, FP64 slower at every order).
+// GB300 (circle pulse, 131072 triangles: 5.26 against 7.41 us per stage; order 2 10.4-12.6
+// against 10.6-10.7, FP64 slower at every order).
 bool one_kernel_stage(const rdg_ctx* ctx) {
   if (ctx->gemm || (ctx->esz == 4 && split_volume32(ctx->N))) return false;
   const bool fast = ctx->esz == 4 && ctx->N == 1;

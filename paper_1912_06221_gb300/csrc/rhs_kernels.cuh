@@ -292,75 +292,105 @@ __device__ __noinline__ void stage_volume_tile(const EdgeArgs<T>& a, int64_t v, 
   stage_out(a.vol + k0 * NP, sh, nk * NP);
 }
 
-// Flux of edge e, flux_e = W_e [u_k1; u_k2] (Nfp values in side 1's face order), with its
-// two element ids.  The gathers hit L2; the operator words are streamed with evict-first
-// 16-byte loads (in the stage kernel a warp reads 512 contiguous bytes per load of its tile).
-// Shared by the stage kernel's edge role and the one-kernel stage, so both give the same bits.
+// Stored operator words of one edge (difference form, see edge_flux_core).
 template <typename T, int N>
-__device__ __forceinline__ void edge_acc(const EdgeArgs<T>& a, int64_t e, T (&acc)[nfp_of(N)], int& k1, int& k2) {
-  constexpr int NP = np_of(N), NFP = nfp_of(N);
-  constexpr int RW = 2 * NP - 1, NWS = NFP * RW + 1;   // stored values per row / per edge
-  using V = Vec16<T>;
-  using VT = typename V::type;
-  constexpr int QW = (NWS + V::n - 1) / V::n;
-  k1 = a.k1[e];
-  k2 = a.k2[e];
-  T u1[NP], u2[NP];
+struct EdgeWords {
+  static constexpr int NWS = nfp_of(N) * (2 * np_of(N) - 1) + 1;   // stored values per edge
+  static constexpr int QW = (NWS + Vec16<T>::n - 1) / Vec16<T>::n;  // 16-byte words per edge
+  typename Vec16<T>::type v[QW];
+};
+
+// The edge's operator words: streamed with evict-first 16-byte loads (in the stage kernel a
+// warp reads 512 contiguous bytes per load of its tile), or kept in L2 for the first
+// keep_tiles tiles.
+template <typename T, int N>
+__device__ __forceinline__ void edge_words(const EdgeArgs<T>& a, int64_t e, EdgeWords<T, N>& w) {
+  using VT = typename Vec16<T>::type;
+  constexpr int QW = EdgeWords<T, N>::QW;
+  const VT* p = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
+  const bool keep = (e >> 5) < a.keep_tiles;
+  const uint64_t pol = keep ? l2_keep_policy() : 0;
+#pragma unroll
+  for (int q = 0; q < QW; ++q) w.v[q] = keep ? ld_keep(p + q * kTile, pol) : ld_stream(p + q * kTile);
+}
+
+// The two elements' rows of edge e (k1, k2 from the edge table; a boundary edge's ghost side
+// sum_m G_m tau_m(t)); a bad index is recorded and its rows left zero.
+template <typename T, int N>
+__device__ __forceinline__ void edge_rows(const EdgeArgs<T>& a, int k1, int k2, T (&u1)[np_of(N)], T (&u2)[np_of(N)]) {
+  constexpr int NP = np_of(N);
 #pragma unroll
   for (int j = 0; j < NP; ++j) u1[j] = u2[j] = T(0);
-  // self-check of the edge table: a bad index is recorded and its access skipped
   if (k1 < 0 || k1 >= a.K || (k2 >= 0 ? k2 >= a.K : (-1 - (int64_t)k2) >= a.B)) {
     report(a.err, kErrBadIndex);
+    return;
+  }
+  const T* p1 = a.u + (int64_t)k1 * NP;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) u1[j] = __ldg(p1 + j);
+  if (k2 >= 0) {
+    const T* p2 = a.u + (int64_t)k2 * NP;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) u2[j] = __ldg(p2 + j);
   } else {
-    const T* p1 = a.u + (int64_t)k1 * NP;
+    const int64_t bb = -1 - (int64_t)k2;
+    const double t = stage_time(a.time);
+    for (int mm = 0; mm < a.frc.nghost; ++mm) {
+      const T tm = (T)tau_of(a.frc.gkind[mm], a.frc.gomega[mm], t);
+      const T* g = a.G + ((int64_t)mm * a.B + bb) * NP;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) u1[j] = __ldg(p1 + j);
-    if (k2 >= 0) {
-      const T* p2 = a.u + (int64_t)k2 * NP;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) u2[j] = __ldg(p2 + j);
-    } else {
-      // ghost side of a boundary edge: g = sum_m G_m tau_m(t)
-      const int64_t bb = -1 - (int64_t)k2;
-      const double t = stage_time(a.time);
-      for (int mm = 0; mm < a.frc.nghost; ++mm) {
-        const T tm = (T)tau_of(a.frc.gkind[mm], a.frc.gomega[mm], t);
-        const T* g = a.G + ((int64_t)mm * a.B + bb) * NP;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) u2[j] += tm * g[j];
-      }
+      for (int j = 0; j < NP; ++j) u2[j] += tm * g[j];
     }
   }
-  // difference form of the stored operator: each row holds the coefficients of
-  // (u1_1 - u_0, ..., u1_{Np-1} - u_0, u2_0 - u_0, ..., u2_{Np-1} - u_0), u_0 = u1_0, and the
-  // edge's last value s = J_f (v.n1) multiplies u_0 in every row
+}
+
+// flux_e = W_e [u1; u2] (Nfp values in side 1's face order) in the difference form of the
+// stored operator: each row holds the coefficients of (u1_1 - u_0, ..., u1_{Np-1} - u_0,
+// u2_0 - u_0, ..., u2_{Np-1} - u_0), u_0 = u1_0, and the edge's last value s = J_f (v.n1)
+// multiplies u_0 in every row.
+template <typename T, int N>
+__device__ __forceinline__ void edge_flux_core(T (&u1)[np_of(N)], T (&u2)[np_of(N)], const EdgeWords<T, N>& w,
+                                               T (&acc)[nfp_of(N)]) {
+  constexpr int NP = np_of(N), NFP = nfp_of(N);
+  constexpr int RW = 2 * NP - 1, NWS = EdgeWords<T, N>::NWS, QW = EdgeWords<T, N>::QW;
+  using V = Vec16<T>;
   const T ub = u1[0];
 #pragma unroll
   for (int j = 1; j < NP; ++j) u1[j] -= ub;
 #pragma unroll
   for (int j = 0; j < NP; ++j) u2[j] -= ub;
-  const VT* w = reinterpret_cast<const VT*>(a.W) + ((e >> 5) * QW) * kTile + (e & 31);
-  const bool keep = (e >> 5) < a.keep_tiles;
-  const uint64_t pol = keep ? l2_keep_policy() : 0;
 #pragma unroll
   for (int r = 0; r < NFP; ++r) acc[r] = T(0);
   T srow = T(0);
 #pragma unroll
   for (int q = 0; q < QW; ++q) {
-    const VT v = keep ? ld_keep(w + q * kTile, pol) : ld_stream(w + q * kTile);
 #pragma unroll
     for (int cc = 0; cc < V::n; ++cc) {
       const int idx = q * V::n + cc;
       if (idx < NWS - 1) {
         const int r = idx / RW, j = idx % RW;
-        acc[r] = fma(V::get(v, cc), j < NP - 1 ? u1[j + 1] : u2[j - (NP - 1)], acc[r]);
+        acc[r] = fma(V::get(w.v[q], cc), j < NP - 1 ? u1[j + 1] : u2[j - (NP - 1)], acc[r]);
       } else if (idx == NWS - 1) {
-        srow = V::get(v, cc);
+        srow = V::get(w.v[q], cc);
       }
     }
   }
 #pragma unroll
   for (int r = 0; r < NFP; ++r) acc[r] = fma(srow, ub, acc[r]);
+}
+
+// Flux of edge e with its two element ids: rows, operator words, arithmetic.  Shared by the
+// stage kernel's edge role and the one-kernel stage, so both give the same bits.
+template <typename T, int N>
+__device__ __forceinline__ void edge_acc(const EdgeArgs<T>& a, int64_t e, T (&acc)[nfp_of(N)], int& k1, int& k2) {
+  constexpr int NP = np_of(N);
+  k1 = a.k1[e];
+  k2 = a.k2[e];
+  T u1[NP], u2[NP];
+  edge_rows<T, N>(a, k1, k2, u1, u2);
+  EdgeWords<T, N> w;
+  edge_words<T, N>(a, e, w);
+  edge_flux_core<T, N>(u1, u2, w, acc);
 }
 
 // Edge role of the stage kernel: edge e (one thread per edge), its flux scattered to the two
@@ -650,12 +680,16 @@ __global__ void __launch_bounds__(lite_block<T, N>(), elem_min_blocks<T, N, true
 // volume term, LIFT, sources and the stage.  An edge's operator is read by both of its
 // elements (the second read mostly hits L2: elements are ordered along a space-filling
 // curve); in exchange the stage is one launch with no face-flux or volume-term round trip,
-// which pays where a stage's work is small against a launch.  Everything it reads may be
-// written by the previous stage, so it waits for the predecessor first.  Modes 0..3 only: its
+// which pays where a stage's work is small against a launch.  The edge ids and operator words
+// are written by no stage, so at order 1 (few registers for them) they are loaded before the
+// dependency wait, overlapping the previous stage's tail, with 8 blocks per SM asked of the
+// compiler (circle pulse, 131072 triangles: 5.26 us per stage, against 5.52 without the early
+// loads and 6.58 with them at the registers the compiler picks; at order 2 the early loads
+// cost 2x); the rows wait for the predecessor.  Modes 0..3 only: its
 // output must not be a buffer that other blocks gather from (the low-storage stage updates its
 // input in place, so it keeps the two-kernel form).
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kElemBlock) elem_fused_kernel(EdgeArgs<T> ea, ElemArgs<T> a) {
+__global__ void __launch_bounds__(kElemBlock, (N == 1 ? 8 : 1)) elem_fused_kernel(EdgeArgs<T> ea, ElemArgs<T> a) {
   static_assert(MODE >= 0 && MODE <= 3, "SSP-RK3 stages and the right-hand side only");
   constexpr int NP = np_of(N), NFP = nfp_of(N);
   constexpr int OLIFT = 4 * NP * NP;
@@ -664,13 +698,31 @@ __global__ void __launch_bounds__(kElemBlock) elem_fused_kernel(EdgeArgs<T> ea, 
   __shared__ __align__(16) T shs[BLK * NP];
   __shared__ __align__(16) T shn[NEED_UN ? BLK * NP : 4];
   __shared__ T tau_s[RDG_MAX_FORCING_TERMS];
+  constexpr bool PRE = N == 1;
   const int64_t k0 = (int64_t)blockIdx.x * BLK;
   const int nk = (int)min((int64_t)BLK, a.K - k0);
   const int tid = threadIdx.x;
   const bool active = tid < nk;
   const int64_t k = active ? k0 + tid : k0;
+  int er[3], kk1[3], kk2[3];
+  EdgeWords<T, N> w[PRE ? 3 : 1];
+  auto edge_ids = [&]() {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      er[f] = a.eref[(int64_t)f * a.K + k];
+      if (er[f] < 0 || (er[f] >> 1) >= a.E) {   // self-check: record and use edge 0 instead
+        report(a.err, kErrBadIndex);
+        er[f] = 0;
+      }
+      kk1[f] = ea.k1[er[f] >> 1];
+      kk2[f] = ea.k2[er[f] >> 1];
+      if constexpr (PRE) edge_words<T, N>(ea, er[f] >> 1, w[f]);
+    }
+  };
+  if constexpr (PRE) edge_ids();
   wait_for_predecessor();
   allow_dependents();
+  if constexpr (!PRE) edge_ids();
   {
     Staged<T, BLK, NP> gs, gn;
     gs.load(a.us + k0 * NP, nk * NP);
@@ -695,18 +747,18 @@ __global__ void __launch_bounds__(kElemBlock) elem_fused_kernel(EdgeArgs<T> ea, 
     const T ij = a.geo[5 * a.K + k];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      int er = a.eref[(int64_t)f * a.K + k];
-      if (er < 0 || (er >> 1) >= a.E) {     // self-check: record and use edge 0 instead
-        report(a.err, kErrBadIndex);
-        er = 0;
+      T acc[NFP], q[NFP], u1[NP], u2[NP];
+      edge_rows<T, N>(ea, kk1[f], kk2[f], u1, u2);
+      if constexpr (PRE) {
+        edge_flux_core<T, N>(u1, u2, w[f], acc);
+      } else {
+        edge_words<T, N>(ea, er[f] >> 1, w[0]);
+        edge_flux_core<T, N>(u1, u2, w[0], acc);
       }
-      T acc[NFP], q[NFP];
-      int k1, k2;
-      edge_acc<T, N>(ea, er >> 1, acc, k1, k2);
       // side 1 in its face order; side 2 (outward normal -n1, face traversed the other way)
       // negated and reversed
 #pragma unroll
-      for (int c = 0; c < NFP; ++c) q[c] = (er & 1) ? -acc[NFP - 1 - c] : acc[c];
+      for (int c = 0; c < NFP; ++c) q[c] = (er[f] & 1) ? -acc[NFP - 1 - c] : acc[c];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         T s = T(0);
