@@ -140,3 +140,28 @@ def test_partition_upload_rejects_unmatched_owned_face():
     with pytest.raises(rdg.RdgError) as e:
         rdg.Solver(xy, tri[:10], 2, 1.0, n_owned=10)
     assert e.value.code == rdg.rdg.RDG_EMESH
+
+
+@pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
+def test_stage_parts_on_an_unsplit_context(prec):
+    """A context uploaded whole: part 0 enqueues nothing, part 1 the whole stage, so parts 0
+    then 1 of every stage equal rdg_rk_step; a part other than 0 or 1 is refused."""
+    xy, tri = unit_square_mesh(8, 0.1, 2)
+    D = np.where(np.arange(tri.shape[0]) % 4 == 0, 1.0, 0.1)
+    a = rdg.Solver(xy, tri, 2, D, v=(0.3, 0.2), precision=prec)
+    b = rdg.Solver(xy, tri, 2, D, v=(0.3, 0.2), precision=prec)
+    assert a.split_counts() == (a.K, a.E)
+    u0 = random_nodal(a.K, a.Np, 3)
+    a.set_state(u0)
+    b.set_state(u0)
+    dt = 1e-5
+    for n in range(4):
+        a.rk_step(n * dt, dt)
+        for st in range(3):
+            b.rk_stage_part(st, 0, n * dt, dt)
+            b.rk_stage_part(st, 1, n * dt, dt)
+    assert np.array_equal(a.get_state_host(), b.get_state_host())
+    with pytest.raises(rdg.RdgError):
+        b.rk_stage_part(0, 2, 0.0, dt)
+    a.close()
+    b.close()
