@@ -17,7 +17,11 @@ times larger (of size |grad u| / h against |lap u|), so a relative error delta i
 operator's entries shows up multiplied by that factor: FP32 storage (delta ~ 6e-8) gives
 about 3e-4, and both FP64 constructions (GPU and oracle, delta ~ 1e-13) agree to about 2e-9
 (measured).  There the bounds are 1e-3 (FP32) and 1e-8 (FP64); the step from the same pulse,
-whose increment dt L u is small beside u, meets the strict tolerances."""
+whose increment dt L u is small beside u, meets the strict tolerances.
+
+The same checks (random field's right-hand side, one step of the pulse) run for order 1 in
+FP32, whose default stage is the one-kernel form, and for the GEMM form of the edge flux at
+order 4 (harmonic rule)."""
 import numpy as np
 import pytest
 
@@ -106,4 +110,75 @@ def test_full_size_rk3_step_sampled_elements(work, prec):
     pp = PatchProblem(w.xy, w.tri, w.N, w.D_elem, step_sample, v=w.v, rings=3, interface="alg1", nbr=nbr)
     want = pp.rk3_step(ud.double().cpu().numpy(), 0.0, dt)
     _check(got, want, TOL[prec])
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def work1():
+    import __graft_entry__
+    __graft_entry__.build()
+    w = circle_pulse(m=M, N=1)
+    nbr = face_neighbours(w.xy, w.tri)
+    K = w.K
+    rng = np.random.default_rng(13)
+    sample = np.unique(np.concatenate([rng.choice(K, 400, replace=False), np.arange(40), np.arange(K - 130, K)]))
+    step_sample = np.unique(np.concatenate([rng.choice(K, 40, replace=False), [0, 1, K - 2, K - 1]]))
+    return w, nbr, sample, step_sample
+
+
+def _gpu_dt(s):
+    x = torch.tensor(random_nodal(s.K, s.Np, 2), dtype=s.dtype, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(30):
+        x /= torch.linalg.vector_norm(x)
+        s.rhs_eval(x, y, 0.0)
+        x, y = y, x
+    return 0.5 * 2.5127 / float(torch.linalg.vector_norm(x))
+
+
+def test_full_size_order1_one_kernel_stage(work1):
+    """Order 1 in FP32 runs its stage as one kernel by default (every element computes its
+    three edges' fluxes; 1017 blocks of 128 elements): a right-hand side of a random field
+    and one SSP-RK3 step of the pulse against the oracle on patches of the full mesh."""
+    w, nbr, sample, step_sample = work1
+    s = rdg.Solver(w.xy, w.tri, 1, w.D_elem, v=w.v, precision=rdg.FP32, interface=rdg.IFACE_ALG1)
+    assert s.stage_form == rdg.STAGE_ONE_KERNEL
+    u = random_nodal(s.K, s.Np, 31)
+    ud = torch.tensor(u, dtype=s.dtype, device="cuda")
+    rd = torch.empty_like(ud)
+    s.rhs_eval(ud, rd, 0.0)
+    pp = PatchProblem(w.xy, w.tri, 1, w.D_elem, sample, v=w.v, rings=1, interface="alg1", nbr=nbr)
+    _check(rd.cpu().numpy()[sample], pp.rhs(ud.double().cpu().numpy(), 0.0), TOL[rdg.FP32])
+    dt = _gpu_dt(s)
+    xyn = s.node_coords()
+    u0 = torch.tensor(w.u0(xyn[..., 0], xyn[..., 1]), dtype=s.dtype, device="cuda")
+    s.set_state(u0)
+    s.rk_step(0.0, dt)
+    got = s.get_state_host()[step_sample]
+    pp3 = PatchProblem(w.xy, w.tri, 1, w.D_elem, step_sample, v=w.v, rings=3, interface="alg1", nbr=nbr)
+    _check(got, pp3.rk3_step(u0.double().cpu().numpy(), 0.0, dt), TOL[rdg.FP32])
+    s.close()
+
+
+def test_full_size_gemm_form(work):
+    """The GEMM form of the edge flux (warp-specialised tcgen05 kernel, split 3xTF32, 1524
+    edge tiles over 152 persistent CTAs, the last tile ragged) with the harmonic interface
+    rule: a random field's right-hand side and one SSP-RK3 step of the pulse against the
+    oracle on patches of the full mesh."""
+    w, nbr, sample, step_sample = work
+    s = rdg.Solver(w.xy, w.tri, w.N, w.D_elem, v=w.v, precision=rdg.FP32_3XTF32, interface=rdg.IFACE_HARMONIC)
+    u = random_nodal(s.K, s.Np, 31)
+    ud = torch.tensor(u, dtype=s.dtype, device="cuda")
+    rd = torch.empty_like(ud)
+    s.rhs_eval(ud, rd, 0.0)
+    pp = PatchProblem(w.xy, w.tri, w.N, w.D_elem, sample, v=w.v, rings=1, interface="harmonic", nbr=nbr)
+    _check(rd.cpu().numpy()[sample], pp.rhs(ud.double().cpu().numpy(), 0.0), TOL[rdg.FP32])
+    dt = _gpu_dt(s)
+    xyn = s.node_coords()
+    u0 = torch.tensor(w.u0(xyn[..., 0], xyn[..., 1]), dtype=s.dtype, device="cuda")
+    s.set_state(u0)
+    s.rk_step(0.0, dt)
+    got = s.get_state_host()[step_sample]
+    pp3 = PatchProblem(w.xy, w.tri, w.N, w.D_elem, step_sample, v=w.v, rings=3, interface="harmonic", nbr=nbr)
+    _check(got, pp3.rk3_step(u0.double().cpu().numpy(), 0.0, dt), TOL[rdg.FP32])
     s.close()
