@@ -389,7 +389,7 @@ def run_ours(args):
     edge_n, edge_ms = st["edge"]
     elem_n, elem_ms = st["elem"]
     E, K, Np, Nfp = s.E, s.K, s.Np, s.Nfp
-    # the survey's algorithmic bytes of one stage (stored operators, state in and out,
+    # the algorithmic bytes of one stage (stored operators, state in and out,
     # coefficients and ids); the stage kernel is the dominant launch
     stage_alg = alg_bytes_per_element(N_ORDER, 4) * K
     # the two kernels' own bytes, intermediates (volume term, face fluxes) included
@@ -424,7 +424,7 @@ def run_ours(args):
                                     "frac": stage_alg / t_stage_s / 1e9 / peak}
 
     # the compute side: measured FMA rates (in-process, this GPU at its current clocks) and
-    # the survey's flops per element per stage, 8 Np^2 + 12 Np Nfp + 12 Np
+    # the flops per element per stage, 8 Np^2 + 12 Np Nfp + 12 Np
     p32, p64 = rdg.peak_fma(local, rdg.FP32), rdg.peak_fma(local, rdg.FP64)
     flops_stage = (8 * Np * Np + 12 * Np * Nfp + 12 * Np) * K
     roof["rhs_roofline"] = {"t_bytes_us": stage_alg / (peak * 1e9) * 1e6, "t_flops_us": flops_stage / p32 * 1e6,
@@ -949,12 +949,11 @@ def run_orders(args):
             default_form = "one_kernel" if s.stage_form == rdg.STAGE_ONE_KERNEL else "two_kernels"
             E, K, Np, Nfp = s.E, s.K, s.Np, N + 1
             w_bytes = E * (Nfp * (2 * Np - 1) + 1) * esz
-            # the headline's accounting at this order and precision: edge pass (operators, edge
-            # ids, face fluxes, stage input, volume term, element coefficients) and element pass
-            # (volume term, stage input, step start in two of three stages, output, ids, 1/J,
-            # face fluxes)
-            # the survey's algorithmic bytes per element (stored operators, state in and out,
-            # coefficients, ids); the two kernels' own bytes (intermediates included) beside
+            # the algorithmic bytes per element (stored operators, state in and out,
+            # coefficients, ids); beside them the two kernels' own bytes at this order and
+            # precision: edge pass (operators, edge ids, face fluxes, stage input, volume term,
+            # element coefficients) and element pass (volume term, stage input, step start in
+            # two of three stages, output, ids, 1/J, face fluxes)
             alg = alg_bytes_per_element(N, esz) * K
             own = (E * ((Nfp * (2 * Np - 1) + 1) * esz + 8 + Nfp * esz) + 2 * K * Np * esz + K * 5 * esz
                    + int(K * ((3 + 2.0 / 3.0) * Np * esz + 12 + esz) + E * Nfp * esz))
