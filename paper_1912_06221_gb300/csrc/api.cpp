@@ -824,6 +824,22 @@ int64_t keep_tiles(const rdg_ctx* ctx) {
 // Volume kernel on a stream forked from `st` and joined back after the edge kernel, so the
 // tensor-core volume term and the HBM-bound operator stream share the SMs.  Works the same
 // eagerly and under graph capture (the fork and join become graph edges).
+// Edges [e0, e1) of a stage's edge arguments (e0 a multiple of the 32-edge operator tile):
+// the edge ids, face ids and operator tiles offset by e0.
+template <typename T>
+EdgeArgs<T> edge_subrange(const rdg_ctx* ctx, const EdgeArgs<T>& ea, int64_t e0, int64_t e1) {
+  EdgeArgs<T> r = ea;
+  const int64_t t0 = e0 / kTile;
+  const int64_t tile_bytes = (int64_t)w_vecs_per_edge(ctx->N, ctx->esz) * kTile * 16;
+  r.k1 = ea.k1 + e0;
+  r.k2 = ea.k2 + e0;
+  r.f12 = ea.f12 + e0;
+  r.W = static_cast<const char*>(ea.W) + t0 * tile_bytes;
+  r.E = e1 - e0;
+  r.keep_tiles = std::max<int64_t>(0, ea.keep_tiles - t0);
+  return r;
+}
+
 int enqueue_split_stage(rdg_ctx* ctx, const EdgeArgs<float>& ea, cudaStream_t st) {
   // created on first use; each one again on a later call if its creation failed
   if (!ctx->side_stream && cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -844,7 +860,7 @@ int enqueue_split_stage(rdg_ctx* ctx, const EdgeArgs<float>& ea, cudaStream_t st
   // the join is recorded even after a failed launch, so a capture never ends with the side
   // stream still attached
   if (cudaEventRecord(ctx->ev_join, ctx->side_stream) != cudaSuccess && rc == RDG_OK) rc = RDG_ECUDA;
-  if (rc == RDG_OK) rc = launch_edge_fb32(ctx->N, ea, st);
+  if (rc == RDG_OK) rc = launch_edge_only32(ctx->N, ea, st);
   if (cudaStreamWaitEvent(st, ctx->ev_join, 0) != cudaSuccess && rc == RDG_OK) rc = RDG_ECUDA;
   return rc;
 }
@@ -893,15 +909,7 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
       else rc = launch_edge_vol64(ctx->N, e0, st);
       return rc;
     }
-    EdgeArgs<T> e1 = ea;
-    const int64_t t0 = ctx->e_split / kTile;
-    const int64_t tile_bytes = (int64_t)w_vecs_per_edge(ctx->N, ctx->esz) * kTile * 16;
-    e1.k1 = ctx->d_k1 + ctx->e_split;
-    e1.k2 = ctx->d_k2 + ctx->e_split;
-    e1.f12 = ctx->d_f12 + ctx->e_split;
-    e1.W = static_cast<const char*>(ctx->d_W) + t0 * tile_bytes;
-    e1.E = ctx->E - ctx->e_split;
-    e1.keep_tiles = std::max<int64_t>(0, ea.keep_tiles - t0);
+    const EdgeArgs<T> e1 = edge_subrange(ctx, ea, ctx->e_split, ctx->E);
     if constexpr (sizeof(T) == 4) rc = launch_edge_only32(ctx->N, e1, st);
     else rc = launch_edge_only64(ctx->N, e1, st);
     if (rc == RDG_OK) {

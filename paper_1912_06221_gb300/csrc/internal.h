@@ -118,7 +118,6 @@ int launch_gemm32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 // beside the edge-only operator stream (kind 2) instead of the fused stage kernel (order 6).
 bool split_volume32(int N);
 int launch_volume32(int N, const EdgeArgs<float>& a, cudaStream_t s);
-int launch_edge_fb32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 // Edge blocks only (fluxes into the face slots), every order and precision.
 int launch_edge_only32(int N, const EdgeArgs<float>& a, cudaStream_t s);
 int launch_edge_only64(int N, const EdgeArgs<double>& a, cudaStream_t s);

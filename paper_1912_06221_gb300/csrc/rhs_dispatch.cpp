@@ -69,14 +69,10 @@ int launch_gemm32(int N, const EdgeArgs<float>& a, cudaStream_t s) {
 }
 
 int launch_volume_f6(const EdgeArgs<float>& a, cudaStream_t s);
-int launch_edge_fb_f6(const EdgeArgs<float>& a, cudaStream_t s);
 
 bool split_volume32(int N) { return N == 6; }
 int launch_volume32(int N, const EdgeArgs<float>& a, cudaStream_t s) {
   return N == 6 ? launch_volume_f6(a, s) : RDG_EINVAL;
-}
-int launch_edge_fb32(int N, const EdgeArgs<float>& a, cudaStream_t s) {
-  return N == 6 ? launch_edge_fb_f6(a, s) : RDG_EINVAL;
 }
 
 int gemm_param_words(int N) { return (2 * np_of(N) + nfp_of(N) + 3 + 3) / 4; }

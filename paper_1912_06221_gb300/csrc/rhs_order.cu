@@ -122,15 +122,12 @@ int RDG_CAT(launch_edge_vol_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<RDG_RE
 }
 
 #if RDG_VGEMM
-// the volume term on the tensor cores, and the edge blocks alone (the stage launches them on
-// two streams so they overlap)
+// the volume term on the tensor cores (the stage launches it on a second stream beside the
+// edge-only blocks, so they overlap)
 int RDG_CAT(launch_volume_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<float>& a, cudaStream_t s) {
   void* vb = nullptr;
   if (cudaGetSymbolAddress(&vb, g_vb) != cudaSuccess) return RDG_ECUDA;
   return gemm::launch_volume_gemm_t<kN>(a, static_cast<const float4*>(vb), s);
-}
-int RDG_CAT(launch_edge_fb_, RDG_CAT(RDG_TAG, RDG_ORDER))(const EdgeArgs<float>& a, cudaStream_t s) {
-  return launch_edge_fb_t<float, kN>(a, s);
 }
 #endif
 
