@@ -942,7 +942,11 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
   }
   if (prof) cudaEventRecord(ev[0], st);
   if constexpr (sizeof(T) == 4) {
-    if (ctx->gemm) rc = launch_gemm32(ctx->N, ea, st);
+    if (ctx->gemm) {
+      EdgeArgs<T> eg = ea;
+      eg.hold_tile = ctx->gemm_hold;
+      rc = launch_gemm32(ctx->N, eg, st);
+    }
     else if (split_volume32(ctx->N) && !ctx->d_Dn) rc = enqueue_split_stage(ctx, ea, st);
     else rc = launch_edge_vol32(ctx->N, ea, st);
   } else {
@@ -1200,6 +1204,15 @@ int rdg_set_stage_form(rdg_ctx* ctx, int form) {
   if (form != RDG_STAGE_AUTO && form != RDG_STAGE_TWO_KERNELS && form != RDG_STAGE_ONE_KERNEL)
     return fail(ctx, RDG_EINVAL, "form must be RDG_STAGE_AUTO, RDG_STAGE_TWO_KERNELS or RDG_STAGE_ONE_KERNEL");
   ctx->stage_form = form;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  return RDG_OK;
+}
+
+int rdg_gemm_hold_tile(rdg_ctx* ctx, int64_t tile) {
+  if (!ctx) return RDG_EINVAL;
+  if (tile < -1) return fail(ctx, RDG_EINVAL, "tile must be >= -1");
+  ctx->gemm_hold = tile + 1;
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   ctx->gexec = nullptr;
   return RDG_OK;

@@ -47,6 +47,7 @@ struct rdg_ctx {
   // device buffers
   int integrator = RDG_INTEGRATOR_SSP_RK3;
   int stage_form = RDG_STAGE_AUTO;     // kernel form of a right-hand-side stage
+  int64_t gemm_hold = 0;               // test hook: GEMM-form edge tile gemm_hold - 1 never released
   bool gemm = false;                // GEMM form of the edge flux (RDG_FP32_3XTF32, N <= kMaxGemmN)
   void* d_W = nullptr;              // tiled per-edge operators, or the GEMM-form parameter records
   int32_t *d_k1 = nullptr, *d_k2 = nullptr, *d_eref = nullptr;

@@ -497,6 +497,7 @@ __device__ __forceinline__ void pipe_producer(const EdgeArgs<float>& a, uint8_t*
   }
   for (int i = grp; t < ntiles; i += P::PG, t += tstep) {
     const int s = i & 1;
+    if (t + 1 == a.hold_tile) break;    // test hook: this tile is never released (group-uniform)
     const int64_t e = t * S::M + tid;
     int k1 = nk1, k2 = nk2;
     const int f12 = nf12;

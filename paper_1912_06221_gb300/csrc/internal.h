@@ -65,6 +65,7 @@ struct EdgeArgs {
   int64_t keep_tiles;  // operator tiles [0, keep_tiles) are loaded evict-last (kept in L2)
   const T* Dn;         // D at the nodes [K][Np] when given so (geo then holds the metric alone), else null
   int64_t Kvol;        // fused form: volume terms of elements [0, Kvol) only (0: all K)
+  int64_t hold_tile;   // test hook of the GEMM form: edge tile hold_tile - 1 is never released (0: none)
 };
 
 // Device error bits reported through rdg_synchronize.

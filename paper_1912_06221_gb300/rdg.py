@@ -66,6 +66,7 @@ SIGNATURES = {
     "rdg_rk_stage_part": (_INT, [_P, _INT, _INT, _D, _D]),
     "rdg_split_counts": (_INT, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "rdg_set_stage_form": (_INT, [_P, _INT]),
+    "rdg_gemm_hold_tile": (_INT, [_P, ctypes.c_int64]),
     "rdg_get_stage_form": (_INT, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rdg_error_quadrature": (_INT, [_P, ctypes.POINTER(_INT), _P]),
     "rdg_error_norms": (_INT, [_P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -326,6 +327,10 @@ class Solver:
     def set_stage_form(self, form: int):
         """STAGE_AUTO (default), STAGE_TWO_KERNELS or STAGE_ONE_KERNEL (rdg_set_stage_form)."""
         self._call("rdg_set_stage_form", int(form))
+
+    def gemm_hold_tile(self, tile: int):
+        """Test hook: GEMM-form edge tile `tile` is never released (-1: none)."""
+        self._call("rdg_gemm_hold_tile", int(tile))
 
     @property
     def stage_form(self) -> int:

@@ -130,3 +130,25 @@ def test_tf32_constant_state_kept_exactly():
         assert np.array_equal(s.get_state_host(), u0)
         s.synchronize()
         s.close()
+
+
+@pytest.mark.parametrize("tile", [0, 3])
+def test_gemm_form_bounded_wait_times_out_and_recovers(tile):
+    """Bounded waits of the warp-specialised GEMM kernel: with one edge tile never released
+    by its producer (test hook), the epilogue's wait for it gives up after 1 s, the CTA aborts
+    its other roles' waits, drains its MMAs and frees its tensor memory, and the next
+    synchronize reports RDG_ETIMEOUT; with the hold removed the same context evaluates the
+    right-hand side correctly again."""
+    s, me, D, _, _ = _pair(4, 24, PERIODIC)     # 1152 triangles, 1728 edges: 14 edge tiles
+    pr = Problem(me, D, v=(0.7, -0.4))
+    u = random_nodal(s.K, s.Np, 5).astype(np.float32).astype(np.float64)
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    rd = torch.empty_like(ud)
+    s.gemm_hold_tile(tile)
+    s.rhs_eval(ud, rd, 0.0)
+    with pytest.raises(rdg.RdgError) as e:
+        s.synchronize()
+    assert e.value.code == rdg.rdg.RDG_ETIMEOUT
+    s.gemm_hold_tile(-1)
+    assert parity_err(_rhs(s, u, 0.0), pr.rhs(u, 0.0)) < 1e-5
+    s.close()
