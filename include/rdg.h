@@ -235,11 +235,13 @@ enum { RDG_STAGE_AUTO = 0, RDG_STAGE_TWO_KERNELS = 1, RDG_STAGE_ONE_KERNEL = 2 }
 int rdg_set_stage_form(rdg_ctx* ctx, int form);
 int rdg_get_stage_form(const rdg_ctx* ctx, int* form);
 
-/* Test hook of the GEMM form's bounded waits (no counterpart in the paper): from the next
- * stage on, edge tile `tile` (128 edges) of every GEMM-form launch is never released by its
- * producer, so the warps that wait for it give up after 1 s, the launch leaves early (its
- * results undefined) and the next rdg_synchronize returns RDG_ETIMEOUT; tile = -1 removes the
- * hold.  Contexts without the GEMM form ignore it.  Errors: RDG_EINVAL for tile < -1. */
+/* Test hook of the tensor-core kernels' bounded waits (no counterpart in the paper): from
+ * the next stage on, tile `tile` of every launch of the context's tensor-core kernel is never
+ * released (the GEMM form of the edge flux: edge tile of 128 edges, never handed to the MMAs
+ * by its producer; FP32 order 6: element tile of 128 elements of the volume term, whose MMAs
+ * are never issued), so the threads that wait for it give up after 1-2 s, the launch leaves
+ * early (its results undefined) and the next rdg_synchronize returns RDG_ETIMEOUT; tile = -1
+ * removes the hold.  Other contexts ignore it.  Errors: RDG_EINVAL for tile < -1. */
 int rdg_gemm_hold_tile(rdg_ctx* ctx, int64_t tile);
 
 /* One step of the resident state from time t with step dt with the selected integrator;

@@ -947,7 +947,11 @@ int enqueue_stage(rdg_ctx* ctx, const void* us, const void* un, void* out, int m
       eg.hold_tile = ctx->gemm_hold;
       rc = launch_gemm32(ctx->N, eg, st);
     }
-    else if (split_volume32(ctx->N) && !ctx->d_Dn) rc = enqueue_split_stage(ctx, ea, st);
+    else if (split_volume32(ctx->N) && !ctx->d_Dn) {
+      EdgeArgs<T> eg = ea;
+      eg.hold_tile = ctx->gemm_hold;
+      rc = enqueue_split_stage(ctx, eg, st);
+    }
     else rc = launch_edge_vol32(ctx->N, ea, st);
   } else {
     rc = launch_edge_vol64(ctx->N, ea, st);

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(128, 1) volume_gemm_kernel(EdgeArgs<float> a, 
     }
     fence_async_smem();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && t + 1 != a.hold_tile) {   // (test hook: a held tile's MMAs are never issued)
       tc_fence_after();
       constexpr uint32_t id1 = idesc_tf32<S::NPAD1>(), id2 = idesc_tf32<S::NPAD2>();
       const uint32_t sa = smem_u32(smem), sb = smem_u32(smem + S::OFF_B);

@@ -84,3 +84,28 @@ def test_order6_fp32_many_tiles_agrees_with_fp64_path():
     s32.synchronize()   # raises if a kernel self-check fired
     s32.close()
     s64.close()
+
+
+def test_volume_gemm_bounded_wait_times_out_and_recovers():
+    """Bounded wait of the order-6 volume kernel: with one element tile's MMAs never issued
+    (test hook), its block's completion wait gives up (1 s, once more for 1 s), the block
+    leaves and frees its tensor memory, and the next synchronize reports RDG_ETIMEOUT; with
+    the hold removed the context evaluates the right-hand side against the oracle again."""
+    xy, tri = unit_square_mesh(12, 0.1, 4)         # 288 triangles: 3 element tiles, the last ragged
+    K = tri.shape[0]
+    D = np.where(np.arange(K) % 5 == 0, 1.0, 0.1)
+    s = rdg.Solver(xy, tri, 6, D, v=(0.4, -0.3), precision=rdg.FP32)
+    pr = Problem(Mesh(xy, tri, 6), D, v=(0.4, -0.3))
+    u = random_nodal(K, s.Np, 8).astype(np.float32).astype(np.float64)
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    rd = torch.empty_like(ud)
+    s.gemm_hold_tile(1)
+    s.rhs_eval(ud, rd, 0.0)
+    with pytest.raises(rdg.RdgError) as e:
+        s.synchronize()
+    assert e.value.code == rdg.rdg.RDG_ETIMEOUT
+    s.gemm_hold_tile(-1)
+    s.rhs_eval(ud, rd, 0.0)
+    s.synchronize()
+    assert parity_err(rd.double().cpu().numpy(), pr.rhs(u, 0.0)) < 1e-5
+    s.close()
