@@ -53,6 +53,7 @@ def parse():
                    help="fp32: stored per-edge operators; tf32: GEMM form on the tensor cores (split 3xTF32)")
     p.add_argument("--serve", action="store_true", help="run the request-stream server instead")
     p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second of the request stream")
     p.add_argument("--serve-slots", type=int, default=32)
     p.add_argument("--serve-setup-workers", type=int, default=6)
     p.add_argument("--batch", action="store_true", help="run the batched uneven workload instead")
@@ -612,7 +613,7 @@ def run_ours(args):
 
 
 def run_serve(args):
-    """Poisson stream of solve requests (rate 200/s, seed 3): jittered periodic meshes of
+    """Poisson stream of solve requests (rate 200/s unless --serve-rate, seed 3): jittered periodic meshes of
     log-uniform size 1e3..1e6 triangles, N in 2..6, element-wise D with a log-uniform contrast
     in [1, 1e4] across a random circle, v in [-1,1]^2, 50..500 SSP-RK3 steps, FP32, 120 GB
     admission budget; FP64 spot check of the requests the stream marks (1%).  Prints one
@@ -623,7 +624,7 @@ def run_serve(args):
     import paper_1912_06221_gb300 as rdg
     from paper_1912_06221_gb300.serve import Server, SolveRequest, latency_stats, solve_alone
     from synth import serve_stream
-    stream = serve_stream(seed=3, nreq=args.serve_requests, rate=200.0, build_mesh=False)
+    stream = serve_stream(seed=3, nreq=args.serve_requests, rate=args.serve_rate, build_mesh=False)
     reqs = []
     for r in stream:
         w = r.workload
@@ -657,9 +658,9 @@ def run_serve(args):
             "max_resident": srv.max_concurrent, "budget_bytes": srv.budget, "fp64_spot_checks": checks,
             "setup_seconds_summed": srv.setup_summary(), "setup_workers": args.serve_setup_workers,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "Poisson stream, rate 200/s, seed 3, %d requests, K log-uniform 1e3..1e6, "
+            "config": {"workload": "Poisson stream, rate %g/s, seed 3, %d requests, K log-uniform 1e3..1e6, "
                                    "N 2..6, D contrast log-uniform 1..1e4 across a random circle, 50..500 steps"
-                                   % args.serve_requests}}
+                                   % (args.serve_rate, args.serve_requests)}}
     print(json.dumps(line), flush=True)
 
 
