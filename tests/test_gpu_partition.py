@@ -49,14 +49,15 @@ def _exchange_all(parts, stage):
             sp.unpack(buf, p, sp.recv_bufs[p])
 
 
-@pytest.mark.parametrize("world", [2, 3])
-@pytest.mark.parametrize("prec", [rdg.FP64, rdg.FP32])
-@pytest.mark.parametrize("bc", [rdg.BC_PERIODIC, rdg.BC_DIRICHLET])
-@pytest.mark.parametrize("overlap", [False, True])
-@pytest.mark.parametrize("N", [3, 6])
+# order 3 in every combination; order 6 (where FP32 runs each stage whole in part 1) on two
+# ranks with periodic boundaries, both precisions, whole and two-part stages
+CASES = ([(w, p, bc, ov, 3) for w in (2, 3) for p in (rdg.FP64, rdg.FP32)
+          for bc in (rdg.BC_PERIODIC, rdg.BC_DIRICHLET) for ov in (False, True)]
+         + [(2, p, rdg.BC_PERIODIC, ov, 6) for p in (rdg.FP64, rdg.FP32) for ov in (False, True)])
+
+
+@pytest.mark.parametrize("world,prec,bc,overlap,N", CASES)
 def test_split_mesh_steps_equal_unsplit(world, prec, bc, overlap, N):
-    if N == 6 and (world == 3 or bc == rdg.BC_DIRICHLET):
-        pytest.skip("order 6 (FP32: a stage that runs whole in part 1) once per precision")
     m, v = (16, (0.7, -0.4)) if N == 3 else (8, (0.7, -0.4))
     xy, tri = unit_square_mesh(m, 0.1, 6)
     K = tri.shape[0]
