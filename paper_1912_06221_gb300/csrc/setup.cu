@@ -180,7 +180,10 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
   constexpr int NP = np_of(N), NFP = nfp_of(N), NW = NFP * 2 * NP, WARPS = setup_warps<N>();
   constexpr int RT = setup_ref_count<N>();
   __shared__ double sR[RT];
-  __shared__ double sVp[WARPS][NP * NP];
+  // the basis at both sides' mapped nodes in one pass of the warp where 2 Np lanes fit (N <= 4),
+  // so the FP64 pipe (the set-up's bound) is not half idle for the table; one side at a time above
+  constexpr bool BOTH = 2 * NP <= 32;
+  __shared__ double sVp[WARPS][(BOTH ? 2 : 1) * NP * NP];
   __shared__ double sK[WARPS][NFP * NP];
   __shared__ double sB[WARPS][NFP * NP];
   __shared__ double sD[WARPS][2 * NP + NFP];   // nodal D: d_j at side j's sub-triangle nodes, then D~_i
@@ -340,13 +343,24 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
     }
     if (!Wt && !Wd) return;
   }
+  if constexpr (BOTH) {
+    if (lane < 2 * NP) {
+      const int sd = lane / NP, nd = lane % NP;
+      const double rn = rr[nd], sn = ss[nd];
+      const double Ar = -(rn + sn) / 2 * al[sd] + (rn + 1) / 2 - (sn + 1) / 2;
+      const double As = -(rn + sn) / 2 * be[sd] - (rn + 1) / 2 + (sn + 1) / 2;
+      simplex_basis_tab<N>(Ar, As, jac, &sVp[warp][sd * NP * NP + nd * NP]);
+    }
+    __syncwarp();
+  }
   for (int side = 0; side < 2; ++side) {
-    if (lane < NP) {
+    if (!BOTH && lane < NP) {
       const double rn = rr[lane], sn = ss[lane];
       const double Ar = -(rn + sn) / 2 * al[side] + (rn + 1) / 2 - (sn + 1) / 2;
       const double As = -(rn + sn) / 2 * be[side] - (rn + 1) / 2 + (sn + 1) / 2;
       simplex_basis_tab<N>(Ar, As, jac, &sVp[warp][lane * NP]);
     }
+    const double* vp = &sVp[warp][BOTH ? side * NP * NP : 0];
     const double* QRV = QV + (2 * side) * NFP * NP;
     const double* QSV = QV + (2 * side + 1) * NFP * NP;
     if (in.iface == RDG_IFACE_ALG1 && nodal) {
@@ -399,7 +413,7 @@ __global__ void __launch_bounds__(32 * setup_warps<N>()) edge_setup_kernel(EdgeS
       const int i = t / NP, j = t % NP;
       double acc = 0.0;
 #pragma unroll 7
-      for (int n = 0; n < NP; ++n) acc = fma(sK[warp][i * NP + n], sVp[warp][n * NP + j], acc);
+      for (int n = 0; n < NP; ++n) acc = fma(sK[warp][i * NP + n], vp[n * NP + j], acc);
       sB[warp][t] = acc;
     }
     __syncwarp();
